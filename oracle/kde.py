@@ -1,0 +1,134 @@
+"""ctypes front end of ``kde_oracle.c`` (FP64 double loop; test infrastructure only).
+
+Every function converts its inputs to contiguous float64 (exact for float32 inputs)
+and calls the C double loop. ``kde`` is the plain definition of Sec. 3,
+K(q) = sum_i exp(-a ||q - x_i||^2) (unnormalised; multiply by 1/n for the paper's
+normalised form). ``avg_rel_err`` is the paper's accuracy metric of Sec. 6.1.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kde_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_SO = os.path.join(_OUT_DIR, "libkdeoracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no fast-math: IEEE double, libm exp)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared",
+                        "-o", tmp, _SRC, "-lm", "-lpthread"], check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, c_int, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            lib.oracle_kde.argtypes = [_D, i64, _D, i64, i64, dbl, _D, c_int]
+            lib.oracle_kde_weighted.argtypes = [_D, _D, i64, _D, i64, i64, dbl, _D, c_int]
+            lib.oracle_kde_self.argtypes = [_D, i64, i64, dbl, _D, c_int]
+            lib.oracle_kde_log.argtypes = [_D, i64, _D, i64, i64, dbl, _D, _D, _D, c_int]
+            for f in (lib.oracle_kde, lib.oracle_kde_weighted, lib.oracle_kde_self, lib.oracle_kde_log):
+                f.restype = c_int
+            _lib = lib
+    return _lib
+
+
+def _f64(a) -> np.ndarray:
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _threads(threads):
+    return int(threads) if threads else (os.cpu_count() or 1)
+
+
+def _check(X, Q):
+    X = _f64(X)
+    Q = _f64(Q)
+    if X.ndim != 2 or Q.ndim != 2 or X.shape[1] != Q.shape[1]:
+        raise ValueError("X (n x d) and Q (m x d) must be 2-D with the same d")
+    return X, Q
+
+
+def kde(X, Q, a: float, threads: int | None = None) -> np.ndarray:
+    """K(q_j) = sum_i exp(-a ||q_j - x_i||^2) for every row q_j of Q (FP64)."""
+    X, Q = _check(X, Q)
+    out = np.empty(Q.shape[0], dtype=np.float64)
+    rc = _load().oracle_kde(_p(X), X.shape[0], _p(Q), Q.shape[0], X.shape[1], float(a), _p(out),
+                            _threads(threads))
+    if rc:
+        raise ValueError("oracle_kde rejected its arguments")
+    return out
+
+
+def kde_weighted(X, W, Q, a: float, threads: int | None = None) -> np.ndarray:
+    """sum_i w_i exp(-a ||q_j - x_i||^2) (the subset estimators' inner sum)."""
+    X, Q = _check(X, Q)
+    W = _f64(W).reshape(-1)
+    if W.shape[0] != X.shape[0]:
+        raise ValueError("W must have n entries")
+    out = np.empty(Q.shape[0], dtype=np.float64)
+    rc = _load().oracle_kde_weighted(_p(X), _p(W), X.shape[0], _p(Q), Q.shape[0], X.shape[1],
+                                     float(a), _p(out), _threads(threads))
+    if rc:
+        raise ValueError("oracle_kde_weighted rejected its arguments")
+    return out
+
+
+def kde_self(X, a: float, threads: int | None = None) -> np.ndarray:
+    """deg(i) = sum_{j != i} exp(-a ||x_i - x_j||^2) (similarity-graph degrees, Sec. 4)."""
+    X = _f64(X)
+    out = np.empty(X.shape[0], dtype=np.float64)
+    rc = _load().oracle_kde_self(_p(X), X.shape[0], X.shape[1], float(a), _p(out), _threads(threads))
+    if rc:
+        raise ValueError("oracle_kde_self rejected its arguments")
+    return out
+
+
+def kde_log(X, Q, a: float, threads: int | None = None):
+    """(log K, d2min, kappa) per query, exact even when every term underflows double."""
+    X, Q = _check(X, Q)
+    m = Q.shape[0]
+    logk, d2min, kappa = (np.empty(m, dtype=np.float64) for _ in range(3))
+    rc = _load().oracle_kde_log(_p(X), X.shape[0], _p(Q), m, X.shape[1], float(a), _p(logk),
+                                _p(d2min), _p(kappa), _threads(threads))
+    if rc:
+        raise ValueError("oracle_kde_log rejected its arguments")
+    return logk, d2min, kappa
+
+
+def rel_err(est, ref) -> np.ndarray:
+    """|est - ref| / |ref| per query (0 where both are 0)."""
+    est = np.asarray(est, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    diff = np.abs(est - ref)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        r = np.where(ref != 0, diff / np.abs(ref), np.where(diff == 0, 0.0, np.inf))
+    return r
+
+
+def avg_rel_err(est, ref) -> float:
+    """The paper's accuracy metric (Sec. 6.1): (1/m) sum_i |mu_i - mu_i*| / mu_i*."""
+    return float(np.mean(rel_err(est, ref)))
