@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Benchmark of exact Gaussian KDE on GB300: kernel evaluations per second (m*n/s).
+
+One step = one pass of the query path over one batch: for each bandwidth of the
+workload, the query matrix (resident in HBM) is evaluated against the resident point
+set (query-side preparation, the pairwise kernel with fused exp and row sum, the FP64
+cross-split combine). Point-set creation (copy + data-side preparation) is a one-off per
+dataset; its time is reported separately as ``create_ms``.
+
+Default workload (N = 1): n = m = 100000, d = 16, 10-component Gaussian mixture (means
+uniform in [-10, 10]^16, std 1), bandwidths a in {0.01, 0.1, 1.0}: 3e10 evaluations
+per step. Inputs fit in L2, so L2 is flushed (a 512 MiB write) between timed steps,
+outside the per-step CUDA-event brackets.
+
+Under torchrun (N > 1) every rank runs the same workload on its own query batch
+(weak scaling over query batches; the point set is replicated, no data-path collective).
+
+--impl reference times the FP64 CPU oracle (the baseline for this method) on the
+host cores, on a bounded sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_07096_gb300 import datagen as G  # noqa: E402
+
+METRIC = "KDE kernel evals/s (m*n/s)"
+UNIT = "evals/s"
+
+WORKLOADS = {
+    # name: (description, builder)
+    "single_d16": "exact Gaussian KDE n=m=100000 d=16 FP32, 10-component mixture means U[-10,10]^16 std 1, a in {0.01,0.1,1.0}",
+    "large_d64": "exact Gaussian KDE n=2000000 m=100000 d=64 FP32, 50-component mixture means U[-10,10]^64 std logU[0.5,2], a=0.05",
+}
+
+
+def build_workload(name, rank=0, n=None, m=None):
+    if name == "single_d16":
+        X, Q = G.workload_single_d16(0, n or 100_000, m or 100_000)
+        if rank:
+            Q = G.sample(G.make_mixture(0, 10, 16, -10.0, 10.0, 1.0), 1000 + rank, Q.shape[0], "query")
+        return X, Q, [0.01, 0.1, 1.0]
+    if name == "large_d64":
+        X, Q, a = G.workload_large_d64(0, n or 2_000_000, m or 100_000)
+        if rank:
+            mix = G.make_mixture(0, 50, 64, -10.0, 10.0, (0.5, 2.0))
+            Q = G.sample(mix, 1000 + rank, Q.shape[0], "query")
+        return X, Q, [a]
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ------------------------------------------------------------------------------------
+# CPU baseline (the FP64 oracle, as it stands)
+# ------------------------------------------------------------------------------------
+def cpu_oracle_rate(X, Q, a, budget_s=12.0, min_q=2):
+    import oracle
+    threads = os.cpu_count() or 1
+    q0 = max(min_q, threads)
+    t = time.perf_counter()
+    oracle.kde(X, Q[:q0], a, threads=threads)
+    dt = time.perf_counter() - t
+    per_q = dt / q0
+    s = int(min(len(Q), max(q0, budget_s / max(per_q, 1e-9))))
+    s = max(threads, (s // threads) * threads) if s >= threads else s
+    t = time.perf_counter()
+    oracle.kde(X, Q[:s], a, threads=threads)
+    dt = time.perf_counter() - t
+    return {"value": s * X.shape[0] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {s} queries x all {X.shape[0]} points, d={X.shape[1]}, a={a}, FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    X, Q, alist = build_workload(args.workload)
+    threads = os.cpu_count() or 1
+    # size each step so that warmup + steps stay within a few minutes
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    per = cpu_oracle_rate(X, Q, alist[0], budget_s=1.0)
+    s = int(max(threads, min(len(Q), budget * per["value"] / X.shape[0] / len(alist))))
+    for _ in range(args.warmup):
+        for a in alist:
+            oracle.kde(X, Q[:threads], a, threads=threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        for a in alist:
+            oracle.kde(X, Q[:s], a, threads=threads)
+    dt = time.perf_counter() - t
+    value = args.steps * len(alist) * s * X.shape[0] / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload],
+                                             "sample_queries_per_step": s, "bandwidths": alist},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{s} queries x {X.shape[0]} points per bandwidth per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Per-SM-per-clock unit counts used for the ALU-bound rooflines:
+FP32_LANES_PER_SM = 128       # FFMA lanes per SM per clock
+EX2_PER_SM_CLK = 32.0         # MUFU ex2 results per SM per clock (measured by the probe)
+SMS = 152
+
+
+def roofline_for(form, d, pairs, ms, clocks, peaks):
+    """Roofline object for the dominant (pairwise) kernel."""
+    f_hz = (clocks.get("sm_mhz") or 1900.0) * 1e6
+    sec = ms * 1e-3
+    if form in ("simt_f32", "simt_f64"):
+        d_pad = 4 * math.ceil(d / 4)
+        ops = pairs * (2 * d_pad + 3)  # FSUB + FFMA per coordinate; FFMA, ex2, FADD per pair
+        peak = FP32_LANES_PER_SM * SMS * f_hz
+        return {"bound": "alu", "achieved": ops / sec / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                "frac": ops / sec / peak, "traffic": None,
+                "note": f"FP32 pipe: (2*{d_pad}+3) ops/pair vs 128 lanes x {SMS} SMs x sampled clock"}
+    # tensor-core form: the slower of the tensor pipe (3 split-FP16 products) and MUFU ex2
+    k_pad = 16 * math.ceil(d / 16)
+    flops = pairs * 2 * 3 * k_pad
+    t_tensor = flops / (peaks["bf16_tflops"] * 1e12)
+    ex2_peak = EX2_PER_SM_CLK * SMS * f_hz
+    t_mufu = pairs / ex2_peak
+    if t_mufu >= t_tensor:
+        return {"bound": "alu", "achieved": pairs / sec / 1e12, "peak": ex2_peak / 1e12, "unit": "Tex2/s",
+                "frac": pairs / sec / ex2_peak, "traffic": None,
+                "tensor_frac": flops / sec / (peaks["bf16_tflops"] * 1e12),
+                "note": "MUFU ex2 bound: one ex2 per pair"}
+    return {"bound": "tensor", "achieved": flops / sec / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": flops / sec / (peaks["bf16_tflops"] * 1e12), "traffic": None,
+            "note": "3 split-FP16 products over K=pad16(d)"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2407_07096_gb300 import build as B
+    from paper_2407_07096_gb300 import _lib as L
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    lib = L.load()
+
+    X, Q, alist = build_workload(args.workload, rank, args.n, args.m)
+    n, d = X.shape
+    m = Q.shape[0]
+    t = time.perf_counter()
+    kdes = [ExactGaussianKDE(X, a, form=args.form) for a in alist]
+    torch.cuda.synchronize()
+    create_ms = 1e3 * (time.perf_counter() - t) / len(alist)
+    form = kdes[0].form
+    for k in kdes:
+        k.reserve(m)
+
+    Qd = torch.from_numpy(Q).to(dev)
+    outs = [torch.empty(m, dtype=torch.float64, device=dev) for _ in alist]
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for k, o in zip(kdes, outs):
+            k.query_dev(Qd, o, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    # timed region: K steps, each bracketed by events on the launching stream; L2 flushed
+    # between steps outside the brackets
+    for k in kdes:
+        k.profile_begin()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lib.stag_kde_launch_count()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lib.stag_kde_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    prof = [k.profile_end() for k in kdes]
+    kern_ms = sum(p[0] for p in prof)
+    kern_launches = sum(p[1] for p in prof)
+    kern_pairs = sum(p[2] for p in prof)
+    if world > 1:
+        t_all = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        total_ms = float(t_all.item())
+    pairs_per_step = float(m) * n * len(alist)
+    value = world * pairs_per_step * args.steps / (total_ms * 1e-3)
+
+    # end to end through the public host API: pinned Q in, pinned out back, every step
+    Qp = torch.from_numpy(Q).pin_memory()
+    outp = [torch.empty(m, dtype=torch.float64).pin_memory() for _ in alist]
+    Qn = Qp.numpy()
+    for k, o in zip(kdes, outp):
+        L.check(lib.stag_kde_query(k._h, Qn.ctypes.data, m, o.numpy().ctypes.data))
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        for k, o in zip(kdes, outp):
+            L.check(lib.stag_kde_query(k._h, Qn.ctypes.data, m, o.numpy().ctypes.data))
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        t_all = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        e2e_s = float(t_all.item())
+    e2e = {"value": world * pairs_per_step * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(len(alist) * Q.nbytes), "d2h_bytes_per_step": int(len(alist) * m * 8),
+           "steps": e2e_steps}
+
+    peaks, peak_kind = load_peaks()
+    roof = roofline_for(form, d, kern_pairs / max(kern_launches, 1), kern_ms / max(kern_launches, 1), clk, peaks)
+    roof["peak_source"] = peak_kind if roof["bound"] == "tensor" else "derived from unit counts x sampled SM clock"
+    roof["kernel_ms_per_launch"] = kern_ms / max(kern_launches, 1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(X, Q, alist[len(alist) // 2], budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if form != "simt_f64" else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.workload], "n": n, "m": m, "d": d, "bandwidths": alist,
+                           "form": form, "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": f"replicas x{world} (query batches)"},
+                "create_ms": create_ms, "gpu_launches": int(launches), "roofline": roof,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}
+        print(json.dumps(line), flush=True)
+    for k in kdes:
+        k.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single_d16", choices=sorted(WORKLOADS))
+    ap.add_argument("--form", default="auto", choices=["auto", "tc", "simt_f32"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--m", type=int, default=None)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

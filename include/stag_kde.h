@@ -1,0 +1,140 @@
+/*
+ * stag_kde.h — exact Gaussian kernel density estimation on one GB300 GPU (sm_103a).
+ *
+ * Computes, for every query q_j of a batch Q against a resident point set X,
+ *
+ *     K(q_j) = sum_{i=1..n} exp(-a * ||q_j - x_i||^2)
+ *
+ * which is the paper's kernel density (Sec. 3) with the Gaussian kernel
+ * k(x) = exp(-a x^2) (Sec. 3), computed exactly ("naive", O(dmn), Sec. 3 and Sec. 6.1)
+ * rather than estimated. The 1/n factor of the paper's definition is applied only when
+ * the `normalise` option is set; by default the unnormalised sum is returned (the form
+ * the similarity-graph degrees of Sec. 4 and the subset estimators of Sec. 3.1 use).
+ * The create/query/destroy life cycle mirrors the paper's ExactGaussianKDE class
+ * (Sec. 5.3: constructor taking the data and a; query of one point or of a matrix).
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are dense row-major, rows = points, `d` contiguous coordinates per row.
+ *   - Host pointers are plain CPU memory (pageable or pinned); device pointers are CUDA
+ *     global memory on the handle's device. Nothing is retained: the library copies X
+ *     at create time; Q and out are used only during the call (host API) or until the
+ *     work queued on the given stream completes (device API).
+ *   - Return codes: 0 on success, a negative STAG_KDE_E* code on failure. Functions
+ *     returning a pointer return NULL on failure. stag_kde_last_error() gives a
+ *     human-readable reason for the calling thread's most recent failure.
+ *   - On failure the output buffer is left untouched (host API).
+ *   - Inputs must be finite with |coordinate| <= 1e15 (so that squared distances are
+ *     finite in FP32); a must be finite and >= 0 (a < 0 would break k(x) in [0, 1],
+ *     Sec. 3). Violations return STAG_KDE_EINVAL.
+ *   - m = 0 is a valid no-op. n >= 1 and d >= 1 are required.
+ *   - A handle may be used by one thread at a time. Results are deterministic: the same
+ *     handle, inputs and options give bitwise-identical outputs on every call.
+ */
+#ifndef STAG_KDE_H
+#define STAG_KDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STAG_KDE_OK 0
+#define STAG_KDE_EINVAL (-1)     /* bad argument (sizes, NULL pointer, non-finite value)  */
+#define STAG_KDE_ENOMEM (-2)     /* device or host allocation failed                       */
+#define STAG_KDE_ECUDA (-3)      /* a CUDA call failed (message has the CUDA error string) */
+#define STAG_KDE_ETIMEDOUT (-4)  /* a bounded wait expired                                 */
+#define STAG_KDE_ECANCELED (-5)  /* request cancelled or server stopped                    */
+#define STAG_KDE_EUNSUPPORTED (-6) /* form not available for this shape / dtype           */
+
+/* Element type of X and Q. */
+#define STAG_KDE_F32 0
+#define STAG_KDE_F64 1
+
+/* Evaluation form ("precision form"). */
+#define STAG_KDE_FORM_AUTO 0     /* library picks (tensor-core form where its error model allows) */
+#define STAG_KDE_FORM_SIMT_F32 1 /* plain FP32 CUDA-core kernel, direct differences              */
+#define STAG_KDE_FORM_TC 2       /* tcgen05/TMEM tensor-core kernel, split-FP16 products         */
+#define STAG_KDE_FORM_SIMT_F64 3 /* FP64 direct differences (for FP64 inputs)                     */
+
+typedef struct stag_kde stag_kde_t; /* opaque handle */
+
+typedef struct stag_kde_opts {
+    int form;       /* STAG_KDE_FORM_*; 0 = AUTO                                    */
+    int normalise;  /* 1: return (1/n) * sum (the paper's K(q)); 0: the plain sum     */
+    int device;     /* CUDA device ordinal; -1 = the calling thread's current device  */
+    int reserved[5];/* must be zero                                                   */
+} stag_kde_opts;
+
+/* Fills *o with the defaults (AUTO form, unnormalised, current device). */
+void stag_kde_opts_init(stag_kde_opts *o);
+
+/*
+ * Creates a handle holding a device copy of X (n x d, FP32, host memory) with
+ * bandwidth a. The caller may free X on return. Default options.
+ * Returns NULL on error (see stag_kde_last_error()).
+ */
+stag_kde_t *stag_kde_create(const float *X, int64_t n, int64_t d, double a);
+
+/*
+ * As stag_kde_create with an explicit element type (STAG_KDE_F32 or STAG_KDE_F64) and
+ * options (NULL = defaults). FP64 data selects STAG_KDE_FORM_SIMT_F64 under AUTO.
+ */
+stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, double a,
+                               const stag_kde_opts *opts);
+
+/*
+ * Synchronous query with host buffers: Q is m x d in the handle's element type (FP32
+ * for stag_kde_create), out receives m doubles. Copies Q to the device, runs the
+ * kernels on the handle's own stream, copies the result back and waits.
+ * Returns 0, or a negative code with out untouched.
+ */
+int stag_kde_query(stag_kde_t *h, const void *Q, int64_t m, double *out);
+
+/*
+ * Asynchronous query on device buffers: dQ (m x d, handle's element type) and dOut
+ * (m doubles) are device pointers on the handle's device; `stream` is a cudaStream_t
+ * (NULL = the legacy default stream). Work is queued and the call returns; dOut is
+ * valid once the stream reaches that point. Only sizes and pointers are validated;
+ * non-finite values in dQ propagate to the outputs instead of being rejected.
+ * Scratch memory is owned by the handle and grown on demand (a growth synchronises the
+ * handle's device); stag_kde_reserve() pre-sizes it, after which the call allocates
+ * nothing for m <= the reserved size.
+ */
+int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, void *stream);
+
+/* Pre-sizes the handle's scratch for queries of up to m rows. */
+int stag_kde_reserve(stag_kde_t *h, int64_t m);
+
+/* Reads back the handle's parameters; any pointer may be NULL. `form` is the form the
+ * handle evaluates with (AUTO resolved). */
+int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *dtype, int *form);
+
+/* Releases the handle and its device memory. NULL-safe. */
+void stag_kde_destroy(stag_kde_t *h);
+
+/* Thread-local description of the calling thread's last failure ("" if none). */
+const char *stag_kde_last_error(void);
+
+/* Library version string. */
+const char *stag_kde_version(void);
+
+/*
+ * Per-handle timing of the main (pairwise) kernel with CUDA events recorded on the
+ * stream it is launched on. stag_kde_profile_begin() enables recording and clears the
+ * record; stag_kde_profile_end() waits for the recorded events, returns the summed
+ * kernel time in milliseconds, the number of main-kernel launches and the number of
+ * query-point pairs they evaluated, and disables recording. Either pointer may be NULL.
+ */
+int stag_kde_profile_begin(stag_kde_t *h);
+int stag_kde_profile_end(stag_kde_t *h, double *ms, int64_t *launches, double *pairs);
+
+/* Number of CUDA kernels this library has launched in this process (all handles,
+ * all threads). Lets a caller count the device work behind a sequence of calls. */
+uint64_t stag_kde_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STAG_KDE_H */

@@ -1,0 +1,120 @@
+// Internal declarations shared by the library's translation units (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/stag_kde.h"
+
+namespace stagkde {
+
+// ---------------------------------------------------------------------------------
+// Error reporting (thread-local last error).
+// ---------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define STAG_CUDA_TRY(expr)                                               \
+    do {                                                                  \
+        cudaError_t _e = (expr);                                          \
+        if (_e != cudaSuccess) return ::stagkde::cuda_fail(_e, #expr);    \
+    } while (0)
+
+// ---------------------------------------------------------------------------------
+// Layout constants of the plain CUDA-core kernel.
+// Points and queries are stored "tile-transposed": tile t of 64 rows is a d_pad x 64
+// block, coordinate k of row r at [t][k][r]. d_pad = d rounded up to 4; the padding
+// coordinates are zero in both X and Q, so they add (0 - 0)^2 = 0 to every distance.
+// ---------------------------------------------------------------------------------
+constexpr int kSimtTile = 64;  // rows per tile (queries per block, points per tile)
+constexpr int kSimtKC = 32;    // coordinates per shared-memory chunk
+
+// Process-wide count of kernel launches (reported by stag_kde_launch_count).
+void count_launch(int k = 1);
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// Per-split partial results: sum (FP64) and an integer power-of-two shift (stored as
+// float). The true partial is sum * 2^shift.
+struct Partials {
+    double *sum = nullptr;
+    float *shift = nullptr;
+    int64_t cap = 0;  // capacity in (split, query) entries
+};
+
+struct TcData;  // tensor-core form data (kde_tc.cu)
+
+}  // namespace stagkde
+
+struct stag_kde {
+    int device = 0;
+    int64_t n = 0, d = 0;
+    double a = 0.0;
+    int dtype = STAG_KDE_F32;
+    int form = STAG_KDE_FORM_SIMT_F32;
+    int normalise = 0;
+    cudaStream_t stream = nullptr;  // the handle's own stream (host API)
+
+    // plain FP32 form: tile-transposed points
+    float *xt = nullptr;
+    int64_t n_tiles = 0;
+    int d_pad = 0;
+
+    // FP64 form: row-major points
+    double *x64 = nullptr;
+
+    // tensor-core form
+    stagkde::TcData *tc = nullptr;
+
+    // scratch (grown on demand, owned by the handle)
+    void *q_dev = nullptr;  // device copy of host queries
+    int64_t q_dev_cap = 0;  // bytes
+    float *qt = nullptr;    // tile-transposed queries
+    int64_t qt_cap = 0;     // floats
+    double *out_dev = nullptr;
+    int64_t out_cap = 0;  // bytes
+    stagkde::Partials part;
+    int *flag_dev = nullptr;  // input-validation flag
+    int *flag_host = nullptr; // pinned mirror
+    int sm_count = 0;
+
+    // main-kernel timing (stag_kde_profile_begin/end)
+    bool profiling = false;
+    std::vector<cudaEvent_t> prof_events;  // start/stop pairs
+    std::vector<cudaEvent_t> prof_pool;    // reusable events
+    int64_t prof_launches = 0;
+    double prof_pairs = 0.0;
+};
+
+namespace stagkde {
+
+// Brackets a main-kernel launch with events when the handle is profiling.
+void prof_start(stag_kde *h, cudaStream_t s);
+void prof_stop(stag_kde *h, cudaStream_t s, double pairs);
+
+// kde_simt.cu
+int simt_prepare_points(stag_kde *h, const float *dX);  // dX: device row-major n x d
+int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s,
+                   int *dflag);
+int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaStream_t s,
+                   int *dflag);
+int ensure_partials(stag_kde *h, int64_t entries);
+int ensure_qt(stag_kde *h, int64_t floats);
+int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s);
+int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s);
+
+// kde_combine.cu
+int launch_combine(const double *part_sum, const float *part_shift, int64_t m, int splits,
+                   double scale, double *out, cudaStream_t s);
+
+// kde_tc.cu
+int tc_prepare_points(stag_kde *h, const float *dX);
+int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag);
+void tc_free(stag_kde *h);
+bool tc_supported(int64_t d);
+
+}  // namespace stagkde

@@ -1,0 +1,411 @@
+// Plain CUDA-core forms of exact Gaussian KDE (Sec. 3: K(q) = sum_i exp(-a ||q - x_i||^2),
+// evaluated over every data point, the "naive" exact method of Sec. 3 / Sec. 6.1).
+//
+//  * kde_simt_f32_kernel: FP32 direct differences sum_k (q_k - x_k)^2, register-tiled
+//    4 queries x 4 points per thread, 64 x 64 pairs per 256-thread block, shared-memory
+//    chunks of 32 coordinates fed by cp.async; the exp and the row sum are fused, so no
+//    m x n matrix is ever written.
+//  * kde_simt_f64_kernel: FP64 direct differences and FP64 exp, for FP64 inputs.
+//
+// Exponent arithmetic (FP32 form). With c = a log2(e), every term is evaluated as
+//     e = 2^(-c d2 - s)      (one fused multiply-add, then ex2.approx)
+// where s is a per-row integer shift, so that terms near the row maximum are computed
+// with a small argument (accurate) and rows whose every term is below FP32's range
+// (a d2 > 87, e.g. d = 128, a = 1) are still represented. s starts at -2^100, which
+// forces the first tile through the rescale path; a tile whose FP32 sum exceeds 2^64
+// (or is not finite) recomputes with s = ceil(max of its exponents) after rescaling
+// the row's accumulators by the exact power of two 2^(s_old - s_new). Terms more than
+// 2^-126 below the shift flush to zero (relative contribution < n 2^-126).
+//
+// Summation: per thread, FP32 over 16 tiles (64 terms), then FP64; the 16 threads that
+// share a row are combined in FP64 with a fixed shuffle pattern; splits of the point set
+// are combined in FP64 by kde_combine.cu. Every order is fixed, so results are
+// bitwise reproducible.
+#include <math.h>
+
+#include "internal.h"
+
+namespace stagkde {
+
+namespace {
+
+constexpr float kShiftFloor = -0x1p100f;  // initial shift (an exact integer)
+constexpr float kOverflowGuard = 0x1p64f;
+constexpr int kFlushTiles = 16;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+__device__ __forceinline__ int clamp_exp(float e) {
+    return (int)fminf(fmaxf(e, -4000.f), 4000.f);
+}
+
+// Row state: value = (acc64 + acc32) * 2^shift.
+struct RowAcc {
+    float shift;
+    float acc32;
+    double acc64;
+};
+
+__device__ __forceinline__ void rescale(RowAcc &r, float s_new) {
+    int de = clamp_exp(r.shift - s_new);  // <= 0
+    r.acc32 = ldexpf(r.acc32, de);
+    r.acc64 = ldexp(r.acc64, de);
+    r.shift = s_new;
+}
+
+// Adds the four terms 2^(negc*d2[j] - shift) (j < valid) to row r.
+__device__ __forceinline__ void add_terms(RowAcc &r, const float d2[4], float negc, int valid) {
+    float ts = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float e = ex2_approx(fmaf(negc, d2[j], -r.shift));
+        ts += (j < valid) ? e : 0.f;
+    }
+    if (!(ts <= kOverflowGuard)) {
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < valid) mx = fmaxf(mx, negc * d2[j]);
+        float s_new = fmaxf(ceilf(mx), kShiftFloor);
+        if (s_new > r.shift) rescale(r, s_new);
+        ts = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float e = ex2_approx(fmaf(negc, d2[j], -r.shift));
+            ts += (j < valid) ? e : 0.f;
+        }
+    }
+    r.acc32 += ts;
+}
+
+__device__ __forceinline__ void merge(RowAcc &r, double oacc, float oshift) {
+    float sm = fmaxf(r.shift, oshift);
+    r.acc64 = ldexp(r.acc64, clamp_exp(r.shift - sm)) + ldexp(oacc, clamp_exp(oshift - sm));
+    r.shift = sm;
+}
+
+template <bool kSingleChunk>
+__global__ void __launch_bounds__(256, 2)
+kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles,
+                    const float *__restrict__ qt, int64_t m, int d_pad, float negc,
+                    int64_t tiles_per_split, double *__restrict__ part_sum,
+                    float *__restrict__ part_shift) {
+    __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
+    __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15;  // point group: points 4*tx .. 4*tx+3 of the tile
+    const int ty = tid >> 4;  // query group: rows 4*ty .. 4*ty+3 of the block
+    const int64_t qtile = blockIdx.x;
+    const int split = blockIdx.y;
+    const int64_t t0 = (int64_t)split * tiles_per_split;
+    const int64_t t1 = min(n_tiles, t0 + tiles_per_split);
+    const int nch = (d_pad + kSimtKC - 1) / kSimtKC;
+    const float *qbase = qt + qtile * (int64_t)d_pad * kSimtTile;
+
+    RowAcc row[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) row[i] = RowAcc{kShiftFloor, 0.f, 0.0};
+
+    auto load = [&](int stage, int64_t t, int ch) {
+        const int k0 = ch * kSimtKC;
+        const int klen = min(kSimtKC, d_pad - k0);
+        const int nvec = klen * (kSimtTile / 4);
+        const float *src = xt + (t * d_pad + k0) * kSimtTile;
+        for (int v = tid; v < nvec; v += 256) cp_async16(&sX[stage][v * 4], src + v * 4);
+        if (!kSingleChunk) {
+            const float *qs = qbase + (int64_t)k0 * kSimtTile;
+            for (int v = tid; v < nvec; v += 256) cp_async16(&sQ[kSingleChunk ? 0 : stage][v * 4], qs + v * 4);
+        }
+    };
+
+    if (kSingleChunk) {
+        const int nvec = d_pad * (kSimtTile / 4);
+        for (int v = tid; v < nvec; v += 256) cp_async16(&sQ[0][v * 4], qbase + v * 4);
+    }
+    const int64_t iters = (t1 - t0) * nch;
+    if (iters > 0) load(0, t0, 0);
+    cp_async_commit();
+
+    float d2[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d2[i][j] = 0.f;
+
+    int group = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int stage = (int)(it & 1);
+        if (it + 1 < iters) {
+            load(stage ^ 1, t0 + (it + 1) / nch, (int)((it + 1) % nch));
+            cp_async_commit();
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+
+        const int ch = (int)(it % nch);
+        const int klen = min(kSimtKC, d_pad - ch * kSimtKC);
+        const float *xs = sX[stage];
+        const float *qs = kSingleChunk ? sQ[0] + ch * kSimtKC * kSimtTile : sQ[kSingleChunk ? 0 : stage];
+#pragma unroll 4
+        for (int k = 0; k < klen; ++k) {
+            const float4 qv = *reinterpret_cast<const float4 *>(&qs[k * kSimtTile + ty * 4]);
+            const float4 xv = *reinterpret_cast<const float4 *>(&xs[k * kSimtTile + tx * 4]);
+            const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+            const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float df = qa[i] - xa[j];
+                    d2[i][j] = fmaf(df, df, d2[i][j]);
+                }
+        }
+        __syncthreads();
+
+        if (ch == nch - 1) {
+            const int64_t t = t0 + it / nch;
+            const int64_t col0 = t * kSimtTile + tx * 4;
+            const int valid = (int)max((int64_t)0, min((int64_t)4, n - col0));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) add_terms(row[i], d2[i], negc, valid);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) d2[i][j] = 0.f;
+            if (++group == kFlushTiles) {
+                group = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    row[i].acc64 += (double)row[i].acc32;
+                    row[i].acc32 = 0.f;
+                }
+            }
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        row[i].acc64 += (double)row[i].acc32;
+        row[i].acc32 = 0.f;
+    }
+    // Combine the 16 threads of the half-warp that share rows 4*ty..4*ty+3.
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double oa = __shfl_xor_sync(0xffffffffu, row[i].acc64, off);
+            const float os = __shfl_xor_sync(0xffffffffu, row[i].shift, off);
+            merge(row[i], oa, os);
+        }
+    }
+    if (tx == 0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int64_t q = qtile * kSimtTile + ty * 4 + i;
+            if (q < m) {
+                part_sum[(int64_t)split * m + q] = row[i].acc64;
+                part_shift[(int64_t)split * m + q] = row[i].shift;
+            }
+        }
+    }
+}
+
+// Row-major n x d -> tile-transposed [tile][d_pad][64], zero padded.
+template <typename T>
+__global__ void to_tiles_kernel(const T *__restrict__ src, int64_t rows, int64_t d, int d_pad,
+                                int64_t n_tiles, float *__restrict__ dst) {
+    const int64_t total = n_tiles * d_pad * kSimtTile;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(idx % kSimtTile);
+        const int64_t rest = idx / kSimtTile;
+        const int k = (int)(rest % d_pad);
+        const int64_t t = rest / d_pad;
+        const int64_t row = t * kSimtTile + r;
+        float v = 0.f;
+        if (row < rows && k < d) v = (float)src[row * d + k];
+        dst[idx] = v;
+    }
+}
+
+template <typename T>
+__global__ void check_finite_kernel(const T *__restrict__ p, int64_t count, int *flag) {
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)p[i];
+        bad |= !(fabs(v) <= 1e15);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+// FP64 form: one thread per query, points staged through shared memory, summed in
+// index order with FP64 exp (plain double arithmetic, for FP64 inputs).
+__global__ void __launch_bounds__(128)
+kde_simt_f64_kernel(const double *__restrict__ X, int64_t n, const double *__restrict__ Q,
+                    int64_t m, int64_t d, double a, double *__restrict__ out) {
+    extern __shared__ double sx[];
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t tp = max((int64_t)1, (int64_t)(4096 / d));  // points per staged tile
+    double s = 0.0;
+    for (int64_t i0 = 0; i0 < n; i0 += tp) {
+        const int64_t cnt = min(tp, n - i0);
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < cnt * d; e += blockDim.x) sx[e] = X[i0 * d + e];
+        __syncthreads();
+        if (j < m) {
+            const double *q = Q + j * d;
+            for (int64_t i = 0; i < cnt; ++i) {
+                double d2 = 0.0;
+                for (int64_t k = 0; k < d; ++k) {
+                    const double t = q[k] - sx[i * d + k];
+                    d2 = fma(t, t, d2);
+                }
+                s += exp(-a * d2);
+            }
+        }
+    }
+    if (j < m) out[j] = s;
+}
+
+int grid_for(int64_t total, int threads) {
+    return (int)std::min<int64_t>(ceil_div(total, threads), 152 * 16);
+}
+
+}  // namespace
+
+int ensure_partials(stag_kde *h, int64_t entries) {
+    if (h->part.cap >= entries) return 0;
+    if (h->part.sum) cudaFree(h->part.sum);
+    if (h->part.shift) cudaFree(h->part.shift);
+    h->part = Partials{};
+    STAG_CUDA_TRY(cudaMalloc(&h->part.sum, entries * sizeof(double)));
+    STAG_CUDA_TRY(cudaMalloc(&h->part.shift, entries * sizeof(float)));
+    h->part.cap = entries;
+    return 0;
+}
+
+int ensure_qt(stag_kde *h, int64_t floats) {
+    if (h->qt_cap >= floats) return 0;
+    if (h->qt) cudaFree(h->qt);
+    h->qt = nullptr;
+    h->qt_cap = 0;
+    STAG_CUDA_TRY(cudaMalloc(&h->qt, floats * sizeof(float)));
+    h->qt_cap = floats;
+    return 0;
+}
+
+int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s) {
+    if (count <= 0) return 0;
+    count_launch();
+    check_finite_kernel<float><<<grid_for(count, 256), 256, 0, s>>>(p, count, dflag);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s) {
+    if (count <= 0) return 0;
+    count_launch();
+    check_finite_kernel<double><<<grid_for(count, 256), 256, 0, s>>>(p, count, dflag);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int simt_prepare_points(stag_kde *h, const float *dX) {
+    h->d_pad = (int)round_up(h->d, 4);
+    h->n_tiles = ceil_div(h->n, kSimtTile);
+    const int64_t total = h->n_tiles * h->d_pad * kSimtTile;
+    STAG_CUDA_TRY(cudaMalloc(&h->xt, total * sizeof(float)));
+    count_launch();
+    to_tiles_kernel<float><<<grid_for(total, 256), 256, 0, h->stream>>>(dX, h->n, h->d, h->d_pad,
+                                                                        h->n_tiles, h->xt);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+// Number of point-set splits: enough blocks for several waves of 2 blocks per SM.
+static int64_t choose_tiles_per_split(const stag_kde *h, int64_t q_tiles) {
+    const int64_t target_blocks = (int64_t)h->sm_count * 2 * 6;
+    int64_t splits = std::max<int64_t>(1, ceil_div(target_blocks, q_tiles));
+    splits = std::min<int64_t>(splits, h->n_tiles);
+    // keep at least 8 tiles (512 points) per split so per-block set-up stays amortised
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, h->n_tiles / 8));
+    return ceil_div(h->n_tiles, splits);
+}
+
+int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s,
+                   int *dflag) {
+    const int64_t q_tiles = ceil_div(m, kSimtTile);
+    int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
+    if (rc) return rc;
+    const int64_t total = q_tiles * h->d_pad * kSimtTile;
+    count_launch();
+    to_tiles_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(dQ, m, h->d, h->d_pad, q_tiles, h->qt);
+    STAG_CUDA_TRY(cudaGetLastError());
+    if (dflag) {
+        rc = launch_check_finite_f32(dQ, m * h->d, dflag, s);
+        if (rc) return rc;
+    }
+    const int64_t tps = choose_tiles_per_split(h, q_tiles);
+    const int64_t splits = ceil_div(h->n_tiles, tps);
+    rc = ensure_partials(h, splits * m);
+    if (rc) return rc;
+    if (q_tiles > 0x7fffffff || splits > 65535) return fail(STAG_KDE_EINVAL, "query batch too large");
+    const float negc = (float)(-h->a * 1.4426950408889634);  // -a log2(e)
+    dim3 grid((unsigned)q_tiles, (unsigned)splits);
+    count_launch();
+    prof_start(h, s);
+    if (h->d_pad <= kSimtKC)
+        kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
+                                                      tps, h->part.sum, h->part.shift);
+    else
+        kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
+                                                       tps, h->part.sum, h->part.shift);
+    prof_stop(h, s, (double)m * (double)h->n);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
+                          dOut, s);
+}
+
+int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag) {
+    if (dflag) {
+        int rc = launch_check_finite_f64(dQ, m * h->d, dflag, s);
+        if (rc) return rc;
+    }
+    const int64_t tp = std::max<int64_t>(1, 4096 / h->d);
+    const size_t smem = (size_t)(tp * h->d) * sizeof(double);
+    if (smem > 48 * 1024) return fail(STAG_KDE_EUNSUPPORTED, "FP64 form: d too large");
+    count_launch();
+    prof_start(h, s);
+    kde_simt_f64_kernel<<<(unsigned)ceil_div(m, 128), 128, smem, s>>>(h->x64, h->n, dQ, m, h->d, h->a, dOut);
+    prof_stop(h, s, (double)m * (double)h->n);
+    STAG_CUDA_TRY(cudaGetLastError());
+    if (h->normalise) {
+        // (1/n) applied by the combine kernel with a single split of FP64 partials
+        int rc = ensure_partials(h, m);
+        if (rc) return rc;
+        STAG_CUDA_TRY(cudaMemcpyAsync(h->part.sum, dOut, m * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        STAG_CUDA_TRY(cudaMemsetAsync(h->part.shift, 0, m * sizeof(float), s));
+        return launch_combine(h->part.sum, h->part.shift, m, 1, 1.0 / (double)h->n, dOut, s);
+    }
+    return 0;
+}
+
+}  // namespace stagkde

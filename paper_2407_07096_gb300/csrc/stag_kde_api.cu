@@ -1,0 +1,357 @@
+// C-ABI of the exact Gaussian KDE library (declared in include/stag_kde.h).
+//
+// The life cycle follows the paper's ExactGaussianKDE (Sec. 5.3): a constructor that
+// takes the data matrix and the bandwidth a, and a query of a matrix of points that
+// returns one density per row. Everything numerical runs in the CUDA kernels of this
+// library; this file validates arguments, owns device memory and streams, and moves
+// data across the host/device boundary.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace stagkde {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return STAG_KDE_ECUDA;
+}
+
+static cudaEvent_t prof_event(stag_kde *h) {
+    if (!h->prof_pool.empty()) {
+        cudaEvent_t e = h->prof_pool.back();
+        h->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void prof_start(stag_kde *h, cudaStream_t s) {
+    if (!h->profiling) return;
+    cudaEvent_t e = prof_event(h);
+    if (!e) return;
+    cudaEventRecord(e, s);
+    h->prof_events.push_back(e);
+}
+
+void prof_stop(stag_kde *h, cudaStream_t s, double pairs) {
+    if (!h->profiling || h->prof_events.size() % 2 == 0) return;
+    cudaEvent_t e = prof_event(h);
+    if (!e) {
+        h->prof_pool.push_back(h->prof_events.back());
+        h->prof_events.pop_back();
+        return;
+    }
+    cudaEventRecord(e, s);
+    h->prof_events.push_back(e);
+    h->prof_launches += 1;
+    h->prof_pairs += pairs;
+}
+
+namespace {
+
+constexpr double kMaxAbs = 1e15;
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+bool host_values_ok(const T *p, int64_t count) {
+    for (int64_t i = 0; i < count; ++i) {
+        const double v = (double)p[i];
+        if (!(fabs(v) <= kMaxAbs)) return false;
+    }
+    return true;
+}
+
+int check_a(double a) {
+    if (!(a >= 0.0) || !isfinite(a)) return fail(STAG_KDE_EINVAL, "bandwidth a must be finite and >= 0");
+    return 0;
+}
+
+void free_handle(stag_kde *h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    tc_free(h);
+    cudaFree(h->xt);
+    cudaFree(h->x64);
+    cudaFree(h->q_dev);
+    cudaFree(h->qt);
+    cudaFree(h->out_dev);
+    cudaFree(h->part.sum);
+    cudaFree(h->part.shift);
+    cudaFree(h->flag_dev);
+    if (h->flag_host) cudaFreeHost(h->flag_host);
+    for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+int resolve_form(int requested, int dtype, int64_t d, int *form) {
+    if (dtype == STAG_KDE_F64) {
+        if (requested != STAG_KDE_FORM_AUTO && requested != STAG_KDE_FORM_SIMT_F64)
+            return fail(STAG_KDE_EUNSUPPORTED, "FP64 data supports only the FP64 form");
+        *form = STAG_KDE_FORM_SIMT_F64;
+        return 0;
+    }
+    switch (requested) {
+        case STAG_KDE_FORM_AUTO:
+            *form = tc_supported(d) ? STAG_KDE_FORM_TC : STAG_KDE_FORM_SIMT_F32;
+            return 0;
+        case STAG_KDE_FORM_SIMT_F32:
+            *form = requested;
+            return 0;
+        case STAG_KDE_FORM_TC:
+            if (!tc_supported(d)) return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form does not support this d");
+            *form = requested;
+            return 0;
+        default:
+            return fail(STAG_KDE_EINVAL, "unknown form");
+    }
+}
+
+int ensure_bytes(void **p, int64_t *cap, int64_t bytes) {
+    if (*cap >= bytes) return 0;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    STAG_CUDA_TRY(cudaMalloc(p, bytes));
+    *cap = bytes;
+    return 0;
+}
+
+int run_query(stag_kde *h, const void *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag) {
+    switch (h->form) {
+        case STAG_KDE_FORM_SIMT_F32:
+            return simt_query_f32(h, (const float *)dQ, m, dOut, s, dflag);
+        case STAG_KDE_FORM_SIMT_F64:
+            return simt_query_f64(h, (const double *)dQ, m, dOut, s, dflag);
+        case STAG_KDE_FORM_TC:
+            return tc_query(h, (const float *)dQ, m, dOut, s, dflag);
+    }
+    return fail(STAG_KDE_EINVAL, "handle has an unknown form");
+}
+
+size_t elem_size(int dtype) { return dtype == STAG_KDE_F64 ? sizeof(double) : sizeof(float); }
+
+}  // namespace
+}  // namespace stagkde
+
+using namespace stagkde;
+
+extern "C" {
+
+void stag_kde_opts_init(stag_kde_opts *o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->form = STAG_KDE_FORM_AUTO;
+    o->normalise = 0;
+    o->device = -1;
+}
+
+stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, double a,
+                               const stag_kde_opts *opts) {
+    stag_kde_opts o;
+    stag_kde_opts_init(&o);
+    if (opts) o = *opts;
+    if (!X) return (set_error("X is NULL"), nullptr);
+    if (n < 1 || d < 1) return (set_error("need n >= 1 and d >= 1"), nullptr);
+    if (d > (1 << 20) || n > ((int64_t)1 << 40)) return (set_error("n or d too large"), nullptr);
+    if (dtype != STAG_KDE_F32 && dtype != STAG_KDE_F64) return (set_error("unknown dtype"), nullptr);
+    if (check_a(a)) return nullptr;
+    const bool ok = dtype == STAG_KDE_F32 ? host_values_ok((const float *)X, n * d)
+                                          : host_values_ok((const double *)X, n * d);
+    if (!ok) return (set_error("X has a non-finite value or |x| > 1e15"), nullptr);
+    int form = 0;
+    if (resolve_form(o.form, dtype, d, &form)) return nullptr;
+
+    stag_kde *h = new (std::nothrow) stag_kde();
+    if (!h) return (set_error("out of host memory"), nullptr);
+    if (o.device < 0) {
+        if (cudaGetDevice(&h->device) != cudaSuccess) {
+            set_error("no CUDA device");
+            delete h;
+            return nullptr;
+        }
+    } else {
+        h->device = o.device;
+    }
+    DeviceGuard g(h->device);
+    h->n = n;
+    h->d = d;
+    h->a = a;
+    h->dtype = dtype;
+    h->form = form;
+    h->normalise = o.normalise ? 1 : 0;
+    auto bail = [&](const char *what, cudaError_t e) -> stag_kde_t * {
+        if (e != cudaSuccess) cuda_fail(e, what);
+        free_handle(h);
+        return nullptr;
+    };
+    cudaError_t e;
+    if (!g.ok) return bail("cudaSetDevice", cudaErrorInvalidDevice);
+    if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess)
+        return bail("cudaDeviceGetAttribute", e);
+    if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail("cudaStreamCreate", e);
+    if ((e = cudaMalloc(&h->flag_dev, sizeof(int))) != cudaSuccess) return bail("cudaMalloc(flag)", e);
+    if ((e = cudaMallocHost(&h->flag_host, sizeof(int))) != cudaSuccess) return bail("cudaMallocHost", e);
+
+    const size_t bytes = (size_t)(n * d) * elem_size(dtype);
+    if (dtype == STAG_KDE_F64) {
+        if ((e = cudaMalloc(&h->x64, bytes)) != cudaSuccess) return bail("cudaMalloc(X)", e);
+        if ((e = cudaMemcpyAsync(h->x64, X, bytes, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+            return bail("cudaMemcpy(X)", e);
+    } else {
+        float *dX = nullptr;
+        if ((e = cudaMalloc(&dX, bytes)) != cudaSuccess) return bail("cudaMalloc(X)", e);
+        int rc = 0;
+        if ((e = cudaMemcpyAsync(dX, X, bytes, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) {
+            cudaFree(dX);
+            return bail("cudaMemcpy(X)", e);
+        }
+        // the plain form's layout is always built: it is also the fallback and the
+        // reference used by the tensor-core form's tests
+        rc = simt_prepare_points(h, dX);
+        if (!rc && form == STAG_KDE_FORM_TC) rc = tc_prepare_points(h, dX);
+        cudaStreamSynchronize(h->stream);
+        cudaFree(dX);
+        if (rc) return bail("prepare", cudaSuccess);
+    }
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail("create", e);
+    return h;
+}
+
+stag_kde_t *stag_kde_create(const float *X, int64_t n, int64_t d, double a) {
+    return stag_kde_create_ex(X, STAG_KDE_F32, n, d, a, nullptr);
+}
+
+int stag_kde_reserve(stag_kde_t *h, int64_t m) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (m < 0) return fail(STAG_KDE_EINVAL, "m < 0");
+    DeviceGuard g(h->device);
+    int rc = ensure_bytes(&h->q_dev, &h->q_dev_cap, std::max<int64_t>(1, m * h->d) * elem_size(h->dtype));
+    if (!rc) rc = ensure_bytes((void **)&h->out_dev, &h->out_cap, std::max<int64_t>(1, m) * 8);
+    if (rc) return rc;
+    if (h->form == STAG_KDE_FORM_SIMT_F32 || h->form == STAG_KDE_FORM_TC) {
+        rc = ensure_qt(h, ceil_div(m, kSimtTile) * h->d_pad * kSimtTile);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+int stag_kde_query(stag_kde_t *h, const void *Q, int64_t m, double *out) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (m < 0) return fail(STAG_KDE_EINVAL, "m < 0");
+    if (m == 0) return 0;
+    if (!Q || !out) return fail(STAG_KDE_EINVAL, "Q or out is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
+    const int64_t qbytes = m * h->d * (int64_t)elem_size(h->dtype);
+    int rc = ensure_bytes(&h->q_dev, &h->q_dev_cap, qbytes);
+    if (rc) return rc;
+    rc = ensure_bytes((void **)&h->out_dev, &h->out_cap, m * 8);
+    if (rc) return rc;
+    STAG_CUDA_TRY(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), h->stream));
+    STAG_CUDA_TRY(cudaMemcpyAsync(h->q_dev, Q, qbytes, cudaMemcpyHostToDevice, h->stream));
+    rc = run_query(h, h->q_dev, m, h->out_dev, h->stream, h->flag_dev);
+    if (rc) {
+        cudaStreamSynchronize(h->stream);
+        return rc;
+    }
+    STAG_CUDA_TRY(cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    STAG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (*h->flag_host) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
+    STAG_CUDA_TRY(cudaMemcpyAsync(out, h->out_dev, m * 8, cudaMemcpyDeviceToHost, h->stream));
+    STAG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return 0;
+}
+
+int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, void *stream) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (m < 0) return fail(STAG_KDE_EINVAL, "m < 0");
+    if (m == 0) return 0;
+    if (!dQ || !dOut) return fail(STAG_KDE_EINVAL, "dQ or dOut is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
+    return run_query(h, dQ, m, dOut, (cudaStream_t)stream, nullptr);
+}
+
+int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *dtype, int *form) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (n) *n = h->n;
+    if (d) *d = h->d;
+    if (a) *a = h->a;
+    if (dtype) *dtype = h->dtype;
+    if (form) *form = h->form;
+    return 0;
+}
+
+void stag_kde_destroy(stag_kde_t *h) { free_handle(h); }
+
+int stag_kde_profile_begin(stag_kde_t *h) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    for (cudaEvent_t e : h->prof_events) h->prof_pool.push_back(e);
+    h->prof_events.clear();
+    h->prof_launches = 0;
+    h->prof_pairs = 0.0;
+    h->profiling = true;
+    return 0;
+}
+
+int stag_kde_profile_end(stag_kde_t *h, double *ms, int64_t *launches, double *pairs) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    DeviceGuard g(h->device);
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < h->prof_events.size(); i += 2) {
+        STAG_CUDA_TRY(cudaEventSynchronize(h->prof_events[i + 1]));
+        float t = 0.f;
+        STAG_CUDA_TRY(cudaEventElapsedTime(&t, h->prof_events[i], h->prof_events[i + 1]));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = h->prof_launches;
+    if (pairs) *pairs = h->prof_pairs;
+    for (cudaEvent_t e : h->prof_events) h->prof_pool.push_back(e);
+    h->prof_events.clear();
+    h->profiling = false;
+    return 0;
+}
+
+const char *stag_kde_last_error(void) { return g_last_error.c_str(); }
+
+const char *stag_kde_version(void) { return "stag-kde-gb300 0.1 (sm_103a)"; }
+
+uint64_t stag_kde_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

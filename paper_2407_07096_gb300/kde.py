@@ -1,0 +1,120 @@
+"""Python front end of the exact Gaussian KDE library (marshalling over the C-ABI only).
+
+``ExactGaussianKDE(X, a)`` mirrors the paper's class of the same name (Sec. 5.3 and
+App. A): it is built from a data matrix and the bandwidth a, and ``query`` returns the
+kernel density of every row of a query matrix,
+    K(q) = sum_i exp(-a ||q - x_i||^2)            (normalise=False, the default)
+    K(q) = (1/n) sum_i exp(-a ||q - x_i||^2)      (normalise=True, Sec. 3's definition)
+All arithmetic happens in the CUDA kernels behind ``libstagkde.so``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+
+def _as_host(a, dtype):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=dtype))
+    if arr.ndim == 1:
+        arr = arr.reshape(1, -1)
+    return arr
+
+
+class ExactGaussianKDE:
+    """Exact Gaussian kernel density over a point set resident on one GPU."""
+
+    def __init__(self, X, a: float, form: str = "auto", normalise: bool = False,
+                 device: int | None = None, dtype=None):
+        lib = L.load()
+        try:
+            import torch
+            if isinstance(X, torch.Tensor):
+                X = X.detach().cpu().numpy()
+        except ImportError:
+            pass
+        X = np.asarray(X)
+        if dtype is None:
+            dtype = np.float64 if X.dtype == np.float64 else np.float32
+        self._np_dtype = np.dtype(dtype)
+        self._dt = L.F64 if self._np_dtype == np.float64 else L.F32
+        Xh = _as_host(X, self._np_dtype)
+        opts = L.Opts()
+        lib.stag_kde_opts_init(ctypes.byref(opts))
+        opts.form = L.FORMS[form]
+        opts.normalise = 1 if normalise else 0
+        opts.device = -1 if device is None else int(device)
+        h = lib.stag_kde_create_ex(Xh.ctypes.data, self._dt, Xh.shape[0], Xh.shape[1], float(a),
+                                   ctypes.byref(opts))
+        if not h:
+            raise L.StagKdeError(L.EINVAL, L.last_error())
+        self._h = ctypes.c_void_p(h)
+        self._lib = lib
+        self.n, self.d, self.a = int(Xh.shape[0]), int(Xh.shape[1]), float(a)
+
+    @property
+    def form(self) -> str:
+        f = ctypes.c_int()
+        L.check(self._lib.stag_kde_info(self._h, None, None, None, None, ctypes.byref(f)))
+        return L.FORM_NAMES[f.value]
+
+    def query(self, Q) -> np.ndarray:
+        """Densities of the rows of Q (host array) as float64, synchronously."""
+        Qh = _as_host(Q, self._np_dtype)
+        if Qh.shape[1] != self.d:
+            raise ValueError(f"Q has d={Qh.shape[1]}, the data has d={self.d}")
+        out = np.empty(Qh.shape[0], dtype=np.float64)
+        L.check(self._lib.stag_kde_query(self._h, Qh.ctypes.data, Qh.shape[0], out.ctypes.data))
+        return out
+
+    def query_dev(self, Q, out=None, stream=None):
+        """Queues the densities of the rows of the CUDA tensor Q into the CUDA float64
+        tensor ``out`` on ``stream`` (a torch.cuda.Stream, default: the current one)."""
+        import torch
+        if not (isinstance(Q, torch.Tensor) and Q.is_cuda and Q.is_contiguous()):
+            raise ValueError("Q must be a contiguous CUDA tensor")
+        if Q.dim() != 2 or Q.shape[1] != self.d:
+            raise ValueError("Q must be m x d")
+        want = torch.float64 if self._dt == L.F64 else torch.float32
+        if Q.dtype != want:
+            raise ValueError(f"Q must be {want}")
+        m = Q.shape[0]
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=Q.device)
+        if out.dtype != torch.float64 or not out.is_cuda or out.numel() < m:
+            raise ValueError("out must be a CUDA float64 tensor with m entries")
+        s = stream if stream is not None else torch.cuda.current_stream(Q.device)
+        L.check(self._lib.stag_kde_query_dev(self._h, Q.data_ptr(), m, out.data_ptr(),
+                                             ctypes.c_void_p(s.cuda_stream)))
+        return out
+
+    def profile_begin(self):
+        L.check(self._lib.stag_kde_profile_begin(self._h))
+
+    def profile_end(self):
+        """(summed main-kernel ms, launches, pairs) since profile_begin (event-timed)."""
+        ms, n, pairs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
+        L.check(self._lib.stag_kde_profile_end(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)))
+        return ms.value, n.value, pairs.value
+
+    def reserve(self, m: int):
+        L.check(self._lib.stag_kde_reserve(self._h, int(m)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.stag_kde_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

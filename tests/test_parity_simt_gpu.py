@@ -1,0 +1,142 @@
+"""Parity of the plain CUDA-core forms (FP32 and FP64) with the FP64 oracle, through
+the C-ABI. Element-by-element per query, at sizes spanning several 64-row tiles with
+ragged tails, plus closed forms and edge cases."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._common import mixture_inputs, tol_f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    from paper_2407_07096_gb300 import build
+    build.build()
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE
+    return ExactGaussianKDE
+
+
+def check_f32(kde_cls, X, Q, a, form="simt_f32"):
+    with kde_cls(X, a, form=form) as kde:
+        got = kde.query(Q)
+    ref = oracle.kde(X, Q, a)
+    _, _, kappa = oracle.kde_log(X, Q, a)
+    err = oracle.rel_err(got, ref)
+    tol = tol_f32(kappa, X.shape[1])
+    bad = np.nonzero(err > tol)[0]
+    assert bad.size == 0, (f"{bad.size} queries above tolerance; worst err {err.max():.3e} "
+                           f"at kappa {kappa[np.argmax(err)]:.1f}")
+    return got, ref, err
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5, 8, 15, 16, 17, 31, 32, 33, 63, 64, 65, 127, 128, 129])
+def test_simt_f32_dims(K, d):
+    X, Q = mixture_inputs(d, 301, 71, d)
+    check_f32(K, X, Q, 1.0 / d)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 130), (63, 5), (64, 64), (65, 129), (4097, 33), (700, 1000)])
+def test_simt_f32_ragged_sizes(K, n, m):
+    X, Q = mixture_inputs(n + m, n, m, 16)
+    check_f32(K, X, Q, 0.1)
+
+
+@pytest.mark.parametrize("a", [0.01, 0.1, 1.0, 10.0])
+def test_simt_f32_bandwidths(K, a):
+    X, Q = mixture_inputs(7, 2000, 300, 8)
+    check_f32(K, X, Q, a)
+
+
+def test_simt_f32_a_zero_is_exactly_n(K):
+    X, Q = mixture_inputs(3, 5000, 100, 7)
+    with K(X, 0.0, form="simt_f32") as kde:
+        assert np.all(kde.query(Q) == 5000.0)
+
+
+def test_simt_f32_underflow_shift(K):
+    # d = 128, a = 1: every FP32 term exp(-a d^2) underflows (nearest d^2 ~ 150);
+    # the per-row shift keeps the sum representable.
+    X, Q = mixture_inputs(9, 3000, 50, 128, k=3, spread=1.0)
+    got, ref, _ = check_f32(K, X, Q, 1.0)
+    assert np.all(ref < 1e-38) and np.all(got > 0)
+
+
+def test_simt_f32_two_point_closed_form(K):
+    # a d^2 = 300 and 310: K = e^-300 (1 + e^-10), far below FP32's range
+    X = np.array([[math.sqrt(300.0), 0.0], [0.0, math.sqrt(310.0)]], dtype=np.float32)
+    Xd = X.astype(np.float64)
+    q = np.zeros((1, 2), dtype=np.float32)
+    want = math.exp(-float(Xd[0, 0] ** 2)) + math.exp(-float(Xd[1, 1] ** 2))
+    with K(X, 1.0, form="simt_f32") as kde:
+        got = kde.query(q)[0]
+    assert abs(got / want - 1) < 1e-4  # kappa ~ 300: FP32 rounding of d^2 dominates
+
+
+def test_simt_f32_lattice_closed_form(K):
+    h, a, d = 0.5, 0.15, 3
+    R = math.sqrt(45.0 / a) + 2.0
+    t = np.arange(-math.ceil(R / h), math.ceil(R / h) + 1) * h
+    g = np.meshgrid(t, t, t, indexing="ij")
+    X = np.stack([x.reshape(-1) for x in g], axis=1).astype(np.float32)  # exact in FP32
+    Q = np.random.default_rng(0).uniform(-1, 1, size=(200, d)).astype(np.float32)
+    want = (math.sqrt(math.pi / a) / h) ** d
+    with K(X, a, form="simt_f32") as kde:
+        got = kde.query(Q)
+    assert np.max(np.abs(got / want - 1)) < 1e-5
+
+
+def test_simt_f32_deterministic_and_dev_path(K):
+    import torch
+    X, Q = mixture_inputs(4, 10000, 777, 16)
+    with K(X, 0.3, form="simt_f32") as kde:
+        a1 = kde.query(Q)
+        a2 = kde.query(Q)
+        out = kde.query_dev(torch.from_numpy(Q).cuda())
+        torch.cuda.synchronize()
+        a3 = out.cpu().numpy()
+    assert np.array_equal(a1, a2) and np.array_equal(a1, a3)
+
+
+def test_normalise_option(K):
+    X, Q = mixture_inputs(5, 999, 40, 6)
+    with K(X, 0.5, form="simt_f32") as k0, K(X, 0.5, form="simt_f32", normalise=True) as k1:
+        assert np.allclose(k1.query(Q), k0.query(Q) / 999, rtol=1e-15, atol=0)
+
+
+def test_non_finite_query_rejected_and_out_untouched(K):
+    from paper_2407_07096_gb300 import _lib as L
+    X, Q = mixture_inputs(6, 100, 10, 4)
+    Q[3, 2] = np.nan
+    with K(X, 0.5, form="simt_f32") as kde:
+        out = np.full(10, -7.0)
+        rc = kde._lib.stag_kde_query(kde._h, Q.ctypes.data, 10, out.ctypes.data)
+        assert rc == L.EINVAL and np.all(out == -7.0)
+        Q[3, 2] = 0.0
+        assert kde._lib.stag_kde_query(kde._h, Q.ctypes.data, 10, out.ctypes.data) == 0
+        assert kde._lib.stag_kde_query(kde._h, Q.ctypes.data, 0, out.ctypes.data) == 0
+
+
+def test_simt_f64_small_workload_matches_oracle(K):
+    from paper_2407_07096_gb300 import datagen as G
+    X, Q, a = G.workload_small_f64(0)
+    with K(X, a) as kde:
+        assert kde.form == "simt_f64"
+        got = kde.query(Q)
+    ref = oracle.kde(X, Q, a)
+    _, _, kappa = oracle.kde_log(X, Q, a)
+    assert np.all(oracle.rel_err(got, ref) <= 1e-15 * (8 + 4 * kappa))
+
+
+@pytest.mark.parametrize("n,m,d", [(1, 1, 1), (65, 3, 33), (513, 100, 600)])
+def test_simt_f64_shapes(K, n, m, d):
+    X, Q = mixture_inputs(n, n, m, d, dtype=np.float64)
+    a = 1.0 / d
+    with K(X, a) as kde:
+        got = kde.query(Q)
+    ref = oracle.kde(X, Q, a)
+    _, _, kappa = oracle.kde_log(X, Q, a)
+    assert np.all(oracle.rel_err(got, ref) <= 1e-15 * (8 + 4 * kappa) * math.sqrt(d))
