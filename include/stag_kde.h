@@ -134,6 +134,36 @@ int stag_kde_profile_end(stag_kde_t *h, double *ms, int64_t *launches, double *p
  * all threads). Lets a caller count the device work behind a sequence of calls. */
 uint64_t stag_kde_launch_count(void);
 
+/*
+ * Allocation-free evaluation. The paper has no counterpart; this is a deployment aid.
+ *
+ * For callers that cannot allocate GPU memory at call time: code running inside its
+ * own memory-pool or allocator callback (a nested cudaMalloc would recurse or
+ * deadlock), latency-critical loops that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause, or processes whose device memory is
+ * budgeted up front. The handle API above allocates (its copy of X and its scratch);
+ * this call allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *
+ * Computes out[j] = sum_i exp(-a ||q_j - x_i||^2) (unnormalised) with the plain FP32
+ * form. dX (n x d), dQ (m x d) and dOut (m doubles) are device pointers on the current
+ * device, row-major, owned by the caller; work is queued on `stream` (a cudaStream_t,
+ * NULL = legacy default stream) and the call returns without waiting.
+ *
+ * Scratch: a fixed 8 MiB array in the library's device memory (every GPU that loads
+ * the library holds it until the process exits) stores the per-split partial sums.
+ * It limits m to at most 699050 queries per call; larger m returns STAG_KDE_EINVAL
+ * with a message saying so. All calls in the process share that array, so calls whose
+ * GPU work overlaps (different streams or host threads) race and give wrong results:
+ * serialise them. The array needs no clearing between calls.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * CUDA stream capture. Returns 0 or a negative STAG_KDE_E* code (sizes, NULL pointers,
+ * a < 0 or non-finite are rejected; values in dX/dQ are not inspected).
+ */
+int stag_kde_eval_noalloc(const float *dX, int64_t n, const float *dQ, int64_t m, int64_t d, double a,
+                          double *dOut, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

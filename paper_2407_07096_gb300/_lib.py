@@ -49,6 +49,7 @@ SIGNATURES = [
     ("stag_kde_version", ctypes.c_char_p, []),
     ("stag_kde_launch_count", ctypes.c_uint64, []),
     ("stag_kde_profile_begin", _INT, [_VP]),
+    ("stag_kde_eval_noalloc", _INT, [_VP, _I64, _VP, _I64, _I64, _DBL, _VP, _VP]),
     ("stag_kde_profile_end", _INT, [_VP, ctypes.POINTER(_DBL), ctypes.POINTER(_I64), ctypes.POINTER(_DBL)]),
 ]
 
