@@ -115,6 +115,7 @@ int launch_combine(const double *part_sum, const float *part_shift, int64_t m, i
 int tc_prepare_points(stag_kde *h, const float *dX);
 int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag);
 void tc_free(stag_kde *h);
+int tc_check_error(stag_kde *h, cudaStream_t s);
 bool tc_supported(int64_t d);
 
 }  // namespace stagkde

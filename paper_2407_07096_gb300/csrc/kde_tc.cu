@@ -1,13 +1,873 @@
-// Tensor-core form (tcgen05/TMEM) of exact Gaussian KDE — see the implementation below.
+// Tensor-core form of exact Gaussian KDE (Sec. 3: K(q) = sum_i exp(-a ||q - x_i||^2)) on
+// sm_103a: tcgen05.mma into TMEM, operands fed by TMA, exp and row sum fused into the
+// epilogue, so the m x n matrix of kernel values never exists in memory.
+//
+// Arithmetic. The point set is cut into tiles of BN points; tile t has a centre c_t
+// (the FP64 mean of its points, stored as FP32) and the queries are centred on the
+// global mean c_g. With v = x - c_t, u = q - c_g and D_t = c_t - c_g,
+//     ||q - x||^2 = ||q - c_t||^2 + ( ||v||^2 + 2 D_t . v ) - 2 u . v        (exact)
+//                 = R(q, t)       +   C(x)                   - 2 u . v
+// R is computed by direct differences in FP32 (rowterm kernel, one value per query and
+// tile), C in FP64 at create time (one value per point), and u . v on the tensor cores
+// with FP16 hi/lo splits of u and v (power-of-two scaled into FP16 range):
+//     u . v ~ u_hi . v_hi + u_hi . v_lo + u_lo . v_hi        (three MMAs, FP32 accumulate)
+// which represents both operands to ~2^-22 and drops only the u_lo . v_lo term (~2^-22).
+// The cancellation of the expansion is confined to the size of ||v|| (the tile radius)
+// and ||u||; the epilogue evaluates, per pair,
+//     e = 2^( kk * D - (c R + s_row) - c C ),   c = a log2(e), kk = 2c / (scale_u scale_v)
+// with the same integer per-row shift s as the plain form (see kde_simt.cu) so that
+// rows whose every term is below FP32's range are still represented.
+//
+// Kernel structure (persistent, one CTA per SM, warp-specialised):
+//   warp 0      TMA producer: per work unit the query tile's A planes (u_hi, u_lo), per
+//               point tile the B planes (v_hi, v_lo) and a metadata block (C of the
+//               tile's points, R of the unit's 128 queries) into rings of stages;
+//   warp 1      allocates TMEM; one thread issues 3 * K/16 MMAs per tile into one of
+//               two TMEM accumulators (128 lanes x BN columns, FP32) and commits;
+//   warps 2..9  epilogue: each thread owns one query row (its TMEM lane) and half of the
+//               tile's columns: tcgen05.ld, two packed FP32 ops, ex2, packed add.
+// A work unit is (query tile of 128 rows, contiguous range of point tiles); the partial
+// sums per (range, query) are combined in FP64 by kde_combine.cu.
+// Every mbarrier wait is bounded (%globaltimer); on expiry the kernel records an error
+// code, makes the other roles stop, waits for its own copies and MMAs, frees TMEM and
+// returns, and the host reports STAG_KDE_ETIMEDOUT.
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "internal.h"
+#include "sm100_ptx.cuh"
 
 namespace stagkde {
 
-bool tc_supported(int64_t) { return false; }
-int tc_prepare_points(stag_kde *, const float *) { return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form not built"); }
-int tc_query(stag_kde *, const float *, int64_t, double *, cudaStream_t, int *) {
-    return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form not built");
+// --------------------------------------------------------------------------------------
+// Host-side data of the tensor-core form.
+// --------------------------------------------------------------------------------------
+struct TcData {
+    int Kp = 0;          // per-split operand width in FP16 elements (16, 32, 64 or 128)
+    int BN = 0;          // points per tile (MMA N)
+    int64_t T = 0;       // number of point tiles
+    int64_t n_pad = 0;   // T * BN
+    __half *b_hi = nullptr, *b_lo = nullptr;  // [n_pad][Kp]
+    float *ccol = nullptr;                    // [T][BN]: c * C(x); +inf for padding points
+    float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
+    float *cg = nullptr;                      // [Kp]: global centre c_g
+    double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
+    unsigned *vmax_bits = nullptr;            // max |v| (float bits)
+    float scale_v = 1.f;                      // power of two
+    CUtensorMap map_bhi, map_blo;
+    // query-side scratch
+    __half *a_hi = nullptr, *a_lo = nullptr;  // [m_cap][Kp]
+    int64_t a_rows_cap = 0;
+    CUtensorMap map_ahi, map_alo;
+    float *rowterm = nullptr;  // [T][m_pad]
+    int64_t rt_cap = 0;        // floats
+    unsigned *qmax_bits = nullptr;  // max |u| over the batch (float bits)
+    float *kk = nullptr;            // [1]: 2c / (scale_u scale_v)
+    int *err = nullptr;             // device error code (timeouts)
+    int *err_host = nullptr;        // pinned mirror
+};
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+constexpr int kErrTimeout = 1;
+constexpr float kShiftFloor = -0x1p100f;
+constexpr float kGuard = 0x1p64f;
+constexpr int BM = 128;  // queries per tile (MMA M, TMEM lanes)
+
+// ------------------------------------------------------------------ layout helpers
+template <int KP>
+struct Geo {
+    static constexpr int CW = KP < 64 ? KP : 64;       // elements per TMA box row / swizzle span
+    static constexpr int CH = KP / CW;                 // chunks along K
+    static constexpr int SPC = CW / 16;                // MMA K-steps per chunk
+    static constexpr uint32_t SW = CW == 16 ? ptx::kSw32 : (CW == 32 ? ptx::kSw64 : ptx::kSw128);
+    static constexpr uint32_t SBO = 8 * CW * 2;        // bytes between 8-row core-matrix groups
+    // byte offset of MMA K-step s inside a plane of `rows` rows
+    __device__ static uint32_t koff(int s, int rows) {
+        return (uint32_t)((s / SPC) * rows * CW * 2 + (s % SPC) * 32);
+    }
+};
+
+template <int KP, int BN, int SB, int SMETA, int AB>
+struct Cfg {
+    static constexpr int A_PLANE = BM * KP * 2;
+    static constexpr int B_PLANE = BN * KP * 2;
+    static constexpr int A_BYTES = 2 * A_PLANE;
+    static constexpr int B_BYTES = 2 * B_PLANE;
+    static constexpr int META_BYTES = BN * 4 + BM * 4;
+    static constexpr int OFF_A = 0;
+    static constexpr int OFF_B = OFF_A + AB * A_BYTES;
+    static constexpr int OFF_META = OFF_B + SB * B_BYTES;
+    static constexpr int OFF_MERGE = OFF_META + SMETA * META_BYTES;
+    static constexpr int OFF_BAR = OFF_MERGE + BM * 16;
+    static constexpr int NBAR = 2 * SB + 2 * SMETA + 2 * AB + 4 + 3;
+    static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
+    static constexpr int BYTES = OFF_MISC + 64;
+    static constexpr int SMEM = BYTES + 1024;  // + alignment slack
+    static constexpr uint32_t TMEM_COLS = 2 * BN;
+    static constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, BN);
+};
+
+struct TcParams {
+    const float *ccol;     // [T][BN]
+    const float *rowterm;  // [T][m_pad]
+    const float *kk;       // device scalar
+    double *part_sum;
+    float *part_shift;
+    int *err;
+    int64_t m, m_pad, T, q_tiles, tiles_per_split, units;
+};
+
+__device__ __forceinline__ int cexp(float e) { return (int)fminf(fmaxf(e, -4000.f), 4000.f); }
+
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
 }
-void tc_free(stag_kde *) {}
+__device__ __forceinline__ void unpack2(uint64_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+struct RowState {
+    float shift;
+    float acc32;
+    double acc64;
+};
+
+// Sum of 2^(kk*D[j] - E - s - col[j]) over 32 columns, rescaling the row if needed.
+__device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32], const float *__restrict__ col,
+                                          float kk, float E) {
+    const uint64_t kk2 = pack2(kk, kk);
+    float nb = -(E + st.shift);
+    uint64_t nb2 = pack2(nb, nb);
+    uint64_t acc2 = 0;  // {0.f, 0.f}
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 c4 = *reinterpret_cast<const float4 *>(col + j);
+        const uint64_t x01 = fma2(kk2, pack2(__uint_as_float(D[j]), __uint_as_float(D[j + 1])),
+                                  sub2(nb2, pack2(c4.x, c4.y)));
+        const uint64_t x23 = fma2(kk2, pack2(__uint_as_float(D[j + 2]), __uint_as_float(D[j + 3])),
+                                  sub2(nb2, pack2(c4.z, c4.w)));
+        float a0, a1, a2, a3;
+        unpack2(x01, a0, a1);
+        unpack2(x23, a2, a3);
+        acc2 = add2(acc2, pack2(ptx::ex2_approx(a0), ptx::ex2_approx(a1)));
+        acc2 = add2(acc2, pack2(ptx::ex2_approx(a2), ptx::ex2_approx(a3)));
+    }
+    float s0, s1;
+    unpack2(acc2, s0, s1);
+    float cs = s0 + s1;
+    if (!(cs <= kGuard)) {
+        // rare: first tile of a row, or a tile whose terms exceed the current shift by 2^64
+        float mx = -INFINITY;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fmaf(kk, __uint_as_float(D[j]), -(E + col[j])));
+        const float s_new = fmaxf(ceilf(mx), kShiftFloor);
+        if (s_new > st.shift) {
+            const int de = cexp(st.shift - s_new);
+            st.acc32 = ldexpf(st.acc32, de);
+            st.acc64 = ldexp(st.acc64, de);
+            st.shift = s_new;
+        }
+        nb = -(E + st.shift);
+        cs = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) cs += ptx::ex2_approx(fmaf(kk, __uint_as_float(D[j]), nb - col[j]));
+    }
+    st.acc32 += cs;
+}
+
+template <int KP, int BN, int SB, int SMETA, int AB>
+__global__ void __launch_bounds__(320, 1)
+kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
+              const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
+              const TcParams p) {
+    using C = Cfg<KP, BN, SB, SMETA, AB>;
+    using G = Geo<KP>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + C::OFF_BAR);
+    uint64_t *full_b = bars;
+    uint64_t *empty_b = full_b + SB;
+    uint64_t *full_m = empty_b + SB;
+    uint64_t *empty_m = full_m + SMETA;
+    uint64_t *a_full = empty_m + SMETA;
+    uint64_t *a_empty = a_full + AB;
+    uint64_t *acc_full = a_empty + AB;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *merge_full = acc_empty + 2;
+    uint64_t *merge_empty = merge_full + 1;
+    uint64_t *drain = merge_empty + 1;
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + C::OFF_MISC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + C::OFF_MISC + 16);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < SB; ++i) {
+            ptx::mbar_init(&full_b[i], 1);
+            ptx::mbar_init(&empty_b[i], 1);
+        }
+        for (int i = 0; i < SMETA; ++i) {
+            ptx::mbar_init(&full_m[i], 1);
+            ptx::mbar_init(&empty_m[i], 8);
+        }
+        for (int i = 0; i < AB; ++i) {
+            ptx::mbar_init(&a_full[i], 1);
+            ptx::mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&acc_full[i], 1);
+            ptx::mbar_init(&acc_empty[i], 8);
+        }
+        ptx::mbar_init(merge_full, 4);
+        ptx::mbar_init(merge_empty, 4);
+        ptx::mbar_init(drain, 1);
+        *abort_flag = 0;
+        ptx::fence_mbar_init();
+        ptx::fence_proxy_async();
+    }
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tensormap(&map_ahi);
+        ptx::prefetch_tensormap(&map_alo);
+        ptx::prefetch_tensormap(&map_bhi);
+        ptx::prefetch_tensormap(&map_blo);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(tmem_holder, C::TMEM_COLS);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *tmem_holder;
+
+    auto timed_out = [&]() {
+        atomicExch(p.err, kErrTimeout);
+        *abort_flag = 1;
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t ucount = 0, tcount = 0;
+            uint32_t issued_a = 0, issued_b = 0, issued_m = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
+                const int64_t split = u / p.q_tiles, qt = u % p.q_tiles;
+                const int64_t t0 = split * p.tiles_per_split;
+                const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
+                const int ab = ucount % AB;
+                if (!ptx::mbar_wait_bounded(&a_empty[ab], ((ucount / AB) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                    timed_out();
+                    ok = false;
+                    break;
+                }
+                uint8_t *abuf = smem + C::OFF_A + ab * C::A_BYTES;
+                ptx::mbar_arrive_expect_tx(&a_full[ab], C::A_BYTES);
+#pragma unroll
+                for (int ch = 0; ch < G::CH; ++ch) {
+                    ptx::tma_load_2d(abuf + ch * BM * G::CW * 2, &map_ahi, ch * G::CW, (int)(qt * BM), &a_full[ab]);
+                    ptx::tma_load_2d(abuf + C::A_PLANE + ch * BM * G::CW * 2, &map_alo, ch * G::CW, (int)(qt * BM),
+                                     &a_full[ab]);
+                }
+                ++issued_a;
+                for (int64_t t = t0; t < t1; ++t, ++tcount) {
+                    const int sb = tcount % SB;
+                    if (!ptx::mbar_wait_bounded(&empty_b[sb], ((tcount / SB) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                        timed_out();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *bbuf = smem + C::OFF_B + sb * C::B_BYTES;
+                    ptx::mbar_arrive_expect_tx(&full_b[sb], C::B_BYTES);
+#pragma unroll
+                    for (int ch = 0; ch < G::CH; ++ch) {
+                        ptx::tma_load_2d(bbuf + ch * BN * G::CW * 2, &map_bhi, ch * G::CW, (int)(t * BN), &full_b[sb]);
+                        ptx::tma_load_2d(bbuf + C::B_PLANE + ch * BN * G::CW * 2, &map_blo, ch * G::CW, (int)(t * BN),
+                                         &full_b[sb]);
+                    }
+                    ++issued_b;
+                    const int ms = tcount % SMETA;
+                    if (!ptx::mbar_wait_bounded(&empty_m[ms], ((tcount / SMETA) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                        timed_out();
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *mbuf = smem + C::OFF_META + ms * C::META_BYTES;
+                    ptx::mbar_arrive_expect_tx(&full_m[ms], C::META_BYTES);
+                    ptx::bulk_load(mbuf, p.ccol + t * BN, BN * 4, &full_m[ms]);
+                    ptx::bulk_load(mbuf + BN * 4, p.rowterm + t * p.m_pad + qt * BM, BM * 4, &full_m[ms]);
+                    ++issued_m;
+                }
+            }
+            if (!ok) {
+                // Let the copies already issued land before the CTA's shared memory is
+                // released: wait for the last armed phase of every stage (bounded).
+                volatile int no_abort = 0;
+                auto drain_ring = [&](uint64_t *full, uint32_t issued, uint32_t depth) {
+                    for (uint32_t i = 0; i < depth && i < issued; ++i) {
+                        const uint32_t j = i + ((issued - 1 - i) / depth) * depth;
+                        ptx::mbar_wait_bounded(&full[i], (j / depth) & 1, 100000000ull, &no_abort);
+                    }
+                };
+                drain_ring(full_b, issued_b, SB);
+                drain_ring(full_m, issued_m, SMETA);
+                drain_ring(a_full, issued_a, AB);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t ucount = 0, tcount = 0;
+            bool ok = true;
+            const uint32_t a0 = ptx::smem_u32(smem + C::OFF_A);
+            const uint32_t b0 = ptx::smem_u32(smem + C::OFF_B);
+            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
+                const int64_t split = u / p.q_tiles;
+                const int64_t t0 = split * p.tiles_per_split;
+                const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
+                const int ab = ucount % AB;
+                if (!ptx::mbar_wait_bounded(&a_full[ab], (ucount / AB) & 1, kWaitLimitNs, abort_flag)) {
+                    timed_out();
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint32_t abase = a0 + ab * C::A_BYTES;
+                for (int64_t t = t0; t < t1; ++t, ++tcount) {
+                    const int acc = tcount & 1;
+                    if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((tcount >> 1) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                        timed_out();
+                        ok = false;
+                        break;
+                    }
+                    const int sb = tcount % SB;
+                    if (!ptx::mbar_wait_bounded(&full_b[sb], (tcount / SB) & 1, kWaitLimitNs, abort_flag)) {
+                        timed_out();
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t bbase = b0 + sb * C::B_BYTES;
+                    const uint32_t d_tmem = tmem_base + acc * BN;
+                    uint32_t accumulate = 0;
+#pragma unroll
+                    for (int prod = 0; prod < 3; ++prod) {
+                        // (u_hi, v_hi), (u_hi, v_lo), (u_lo, v_hi)
+                        const uint32_t ap = abase + (prod == 2 ? C::A_PLANE : 0);
+                        const uint32_t bp = bbase + (prod == 1 ? C::B_PLANE : 0);
+#pragma unroll
+                        for (int s = 0; s < KP / 16; ++s) {
+                            const uint64_t ad = ptx::smem_desc(ap + G::koff(s, BM), 16, G::SBO, G::SW);
+                            const uint64_t bd = ptx::smem_desc(bp + G::koff(s, BN), 16, G::SBO, G::SW);
+                            ptx::mma_f16(d_tmem, ad, bd, C::IDESC, accumulate);
+                            accumulate = 1;
+                        }
+                    }
+                    ptx::mma_commit(&empty_b[sb]);
+                    ptx::mma_commit(&acc_full[acc]);
+                }
+                if (ok) ptx::mma_commit(&a_empty[ab]);
+            }
+            // every MMA issued by this thread must finish before TMEM is released
+            volatile int no_abort = 0;
+            ptx::mma_commit(drain);
+            ptx::mbar_wait_bounded(drain, 0, 100000000ull, &no_abort);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue (8 warps)
+        const int ew = warp - 2;             // 0..7
+        const int quad = warp & 3;           // TMEM lane quadrant this warp may access
+        const int half = ew >> 2;            // column half
+        const int row = quad * 32 + lane;    // query row within the tile
+        const float kk = *p.kk;
+        float *merge = reinterpret_cast<float *>(smem + C::OFF_MERGE);
+        uint32_t tcount = 0, ucount = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            const int64_t split = u / p.q_tiles, qt = u % p.q_tiles;
+            const int64_t t0 = split * p.tiles_per_split;
+            const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
+            RowState st{kShiftFloor, 0.f, 0.0};
+            for (int64_t t = t0; t < t1; ++t, ++tcount) {
+                const int acc = tcount & 1;
+                const int ms = tcount % SMETA;
+                // every lane waits; the outcome is made warp-uniform so that the warp never
+                // splits around the __syncwarp calls below
+                bool got = ptx::mbar_wait_bounded(&acc_full[acc], (tcount >> 1) & 1, kWaitLimitNs, abort_flag) &&
+                           ptx::mbar_wait_bounded(&full_m[ms], (tcount / SMETA) & 1, kWaitLimitNs, abort_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    timed_out();
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_BYTES);
+                const float E = meta[BN + row];
+                const float *col = meta + half * (BN / 2);
+                const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + half * (BN / 2);
+                constexpr int NCH = BN / 2 / 32;
+#pragma unroll
+                for (int c = 0; c < NCH; c += 2) {
+                    uint32_t D0[32], D1[32];
+                    ptx::tmem_ld_32x32b_x32(taddr + c * 32, D0);
+                    if (c + 1 < NCH) ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, D1);
+                    ptx::tmem_ld_wait();
+                    if (c + 2 >= NCH) {
+                        // every TMEM column of this buffer has been read: hand it back
+                        ptx::tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+                    }
+                    epi_chunk(st, D0, col + c * 32, kk, E);
+                    if (c + 1 < NCH) epi_chunk(st, D1, col + (c + 1) * 32, kk, E);
+                }
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&empty_m[ms]);
+                st.acc64 += (double)st.acc32;
+                st.acc32 = 0.f;
+            }
+            if (!ok) break;
+            // merge the two column halves of each row (half 1 hands its sums to half 0
+            // through shared memory), then store the unit's partials
+            double *msum = reinterpret_cast<double *>(merge);
+            float *mshift = merge + 2 * BM;
+            if (half == 1) {
+                const bool got = ptx::mbar_wait_bounded(merge_empty, (ucount & 1) ^ 1, kWaitLimitNs, abort_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    timed_out();
+                    break;
+                }
+                msum[row] = st.acc64;
+                mshift[row] = st.shift;
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(merge_full);
+            } else {
+                const bool got = ptx::mbar_wait_bounded(merge_full, ucount & 1, kWaitLimitNs, abort_flag);
+                if (!__all_sync(0xffffffffu, got)) {
+                    timed_out();
+                    break;
+                }
+                const double oa = msum[row];
+                const float os = mshift[row];
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(merge_empty);
+                const float sm = fmaxf(st.shift, os);
+                const double tot = ldexp(st.acc64, cexp(st.shift - sm)) + ldexp(oa, cexp(os - sm));
+                const int64_t q = qt * BM + row;
+                if (q < p.m) {
+                    p.part_sum[split * p.m + q] = tot;
+                    p.part_shift[split * p.m + q] = sm;
+                }
+            }
+            ++ucount;
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, C::TMEM_COLS);
+    }
+}
+
+// ------------------------------------------------------------------ prep kernels
+// Per-tile FP64 coordinate sums and FP32 centres (mean of the tile's real points).
+__global__ void tc_centres_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
+                                  double *__restrict__ tsum, float *__restrict__ cent) {
+    const int64_t t = blockIdx.x;
+    const int64_t r0 = t * BN;
+    const int64_t cnt = min((int64_t)BN, n - r0);
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        double s = 0.0;
+        if (k < d)
+            for (int64_t r = 0; r < cnt; ++r) s += (double)X[(r0 + r) * d + k];
+        tsum[t * Kp + k] = s;
+        cent[t * Kp + k] = (k < d && cnt > 0) ? (float)(s / (double)cnt) : 0.f;
+    }
+}
+
+// Global centre c_g = (sum over tiles of the tile sums) / n, in FP64, fixed order.
+__global__ void tc_global_centre_kernel(const double *__restrict__ tsum, int64_t T, int Kp, int64_t n, int64_t d,
+                                        float *__restrict__ cg) {
+    for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
+        double s = 0.0;
+        for (int64_t t = 0; t < T; ++t) s += tsum[t * Kp + k];
+        cg[k] = k < d ? (float)(s / (double)n) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned *bits, float v) {
+    atomicMax(bits, __float_as_uint(fabsf(v)));
+}
+
+// max over points of |x - c_t| (each coordinate)
+__global__ void tc_vmax_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
+                               const float *__restrict__ cent, unsigned *vmax) {
+    float mx = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * d; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / d, k = i % d;
+        mx = fmaxf(mx, fabsf(X[i] - cent[(r / BN) * Kp + k]));
+    }
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(vmax, mx);
+}
+
+__device__ __forceinline__ float pow2_scale(unsigned maxbits) {
+    // largest power of two s with max * s <= 2^14 (FP16 headroom for hi + lo sums)
+    const float mx = __uint_as_float(maxbits);
+    if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+    int e;
+    frexpf(mx, &e);  // mx in [2^(e-1), 2^e)
+    return ldexpf(1.f, 14 - e);
+}
+
+// FP16 hi/lo split of v = (x - c_t) * scale_v and the column term c * (|v~|^2 + 2 D_t . v~)
+// computed in FP64 from the represented v~ = (hi + lo) / scale_v.
+__global__ void tc_split_points_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp, int64_t n_pad,
+                                       const float *__restrict__ cent, const float *__restrict__ cg,
+                                       const unsigned *__restrict__ vmax, double c, __half *__restrict__ bhi,
+                                       __half *__restrict__ blo, float *__restrict__ ccol) {
+    const float sv = pow2_scale(*vmax);
+    const double inv = 1.0 / (double)sv;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / BN;
+        double nv2 = 0.0, dv = 0.0;
+        for (int k = 0; k < Kp; ++k) {
+            __half h = __float2half_rn(0.f), l = __float2half_rn(0.f);
+            if (i < n && k < d) {
+                const float ct = cent[t * Kp + k];
+                const double v = ((double)X[i * d + k] - (double)ct) * (double)sv;
+                h = __double2half(v);
+                l = __double2half(v - (double)__half2float(h));
+                const double vr = ((double)__half2float(h) + (double)__half2float(l)) * inv;
+                nv2 += vr * vr;
+                dv += ((double)ct - (double)cg[k]) * vr;
+            }
+            bhi[i * Kp + k] = h;
+            blo[i * Kp + k] = l;
+        }
+        ccol[i] = i < n ? (float)(c * (nv2 + 2.0 * dv)) : INFINITY;
+    }
+}
+
+__global__ void tc_qmax_kernel(const float *__restrict__ Q, int64_t m, int64_t d, const float *__restrict__ cg,
+                               unsigned *qmax) {
+    float mx = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m * d; i += (int64_t)gridDim.x * blockDim.x)
+        mx = fmaxf(mx, fabsf(Q[i] - cg[i % d]));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(qmax, mx);
+}
+
+// FP16 hi/lo split of u = (q - c_g) * scale_u for m_pad rows (padding rows zero), and
+// kk = 2c / (scale_u scale_v).
+__global__ void tc_split_queries_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
+                                        const float *__restrict__ cg, const unsigned *__restrict__ qmax,
+                                        const unsigned *__restrict__ vmax, double c, __half *__restrict__ ahi,
+                                        __half *__restrict__ alo, float *__restrict__ kk) {
+    const float su = pow2_scale(*qmax);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *kk = (float)(2.0 * c / ((double)su * (double)pow2_scale(*vmax)));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_pad * Kp;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / Kp;
+        const int k = (int)(i % Kp);
+        __half h = __float2half_rn(0.f), l = __float2half_rn(0.f);
+        if (r < m && k < d) {
+            const double u = ((double)Q[r * d + k] - (double)cg[k]) * (double)su;
+            h = __double2half(u);
+            l = __double2half(u - (double)__half2float(h));
+        }
+        ahi[i] = h;
+        alo[i] = l;
+    }
+}
+
+// R[t][q] = c * ||q - c_t||^2 by direct differences in FP32 (padding queries: 0).
+// One block per (128-query tile, group of point tiles); queries staged transposed.
+__global__ void __launch_bounds__(128)
+tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
+                  const float *__restrict__ cent, int64_t T, int tiles_per_block, float c, float *__restrict__ R) {
+    extern __shared__ float sq[];  // [Kp][128]
+    const int64_t q0 = (int64_t)blockIdx.x * 128;
+    const int r = threadIdx.x;
+    for (int k = 0; k < Kp; ++k) {
+        const int64_t q = q0 + r;
+        sq[k * 128 + r] = (q < m && k < d) ? Q[q * d + k] : 0.f;
+    }
+    __syncthreads();
+    const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
+    const int64_t tb = min(T, ta + tiles_per_block);
+    const bool real = q0 + r < m;
+    for (int64_t t = ta; t < tb; ++t) {
+        const float4 *ct = reinterpret_cast<const float4 *>(cent + t * Kp);
+        float s0 = 0.f, s1 = 0.f;
+        for (int k4 = 0; k4 < Kp / 4; ++k4) {
+            const float4 cv = __ldg(ct + k4);
+            const float d0 = sq[(4 * k4 + 0) * 128 + r] - cv.x;
+            const float d1 = sq[(4 * k4 + 1) * 128 + r] - cv.y;
+            const float d2 = sq[(4 * k4 + 2) * 128 + r] - cv.z;
+            const float d3 = sq[(4 * k4 + 3) * 128 + r] - cv.w;
+            s0 = fmaf(d0, d0, s0);
+            s1 = fmaf(d1, d1, s1);
+            s0 = fmaf(d2, d2, s0);
+            s1 = fmaf(d3, d3, s1);
+        }
+        R[t * m_pad + q0 + r] = real ? c * (s0 + s1) : 0.f;
+    }
+}
+
+// ------------------------------------------------------------------ host helpers
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    });
+    return fn;
+}
+
+// 2-D FP16 tensor map over a [rows][Kp] plane with box {min(Kp,64), box_rows}.
+int make_map(CUtensorMap *map, void *base, int64_t rows, int Kp, int box_rows) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return fail(STAG_KDE_ECUDA, "cuTensorMapEncodeTiled unavailable");
+    const int cw = Kp < 64 ? Kp : 64;
+    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    cuuint32_t box[2] = {(cuuint32_t)cw, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    const CUtensorMapSwizzle sw = cw == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                           : (cw == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(STAG_KDE_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return 0;
+}
+
+int kp_for(int64_t d) {
+    if (d <= 16) return 16;
+    if (d <= 32) return 32;
+    if (d <= 64) return 64;
+    if (d <= 128) return 128;
+    return 0;
+}
+
+int bn_for(int Kp) { return Kp >= 128 ? 128 : 256; }
+
+int grid_for(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_div(total, threads), 152 * 16); }
+
+template <int KP, int BN, int SB, int SMETA, int AB>
+int launch_tc(stag_kde *h, const TcParams &prm, cudaStream_t s) {
+    using C = Cfg<KP, BN, SB, SMETA, AB>;
+    auto kern = kde_tc_kernel<KP, BN, SB, SMETA, AB>;
+    static_assert(C::SMEM <= 232448, "shared memory budget");
+    // at least 116 KB so that no two CTAs share an SM (each holds up to 512 TMEM columns)
+    const int smem = std::max(C::SMEM, 118 * 1024);
+    STAG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int grid = (int)std::min<int64_t>(prm.units, h->sm_count);
+    TcData *tc = h->tc;
+    count_launch();
+    prof_start(h, s);
+    kern<<<grid, 320, smem, s>>>(tc->map_ahi, tc->map_alo, tc->map_bhi, tc->map_blo, prm);
+    prof_stop(h, s, (double)prm.m * (double)h->n);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+}  // namespace
+
+bool tc_supported(int64_t d) { return kp_for(d) != 0; }
+
+void tc_free(stag_kde *h) {
+    TcData *tc = h->tc;
+    if (!tc) return;
+    cudaFree(tc->b_hi);
+    cudaFree(tc->b_lo);
+    cudaFree(tc->ccol);
+    cudaFree(tc->cent);
+    cudaFree(tc->cg);
+    cudaFree(tc->tsum);
+    cudaFree(tc->vmax_bits);
+    cudaFree(tc->a_hi);
+    cudaFree(tc->a_lo);
+    cudaFree(tc->rowterm);
+    cudaFree(tc->qmax_bits);
+    cudaFree(tc->kk);
+    cudaFree(tc->err);
+    if (tc->err_host) cudaFreeHost(tc->err_host);
+    delete tc;
+    h->tc = nullptr;
+}
+
+int tc_prepare_points(stag_kde *h, const float *dX) {
+    TcData *tc = new (std::nothrow) TcData();
+    if (!tc) return fail(STAG_KDE_ENOMEM, "out of host memory");
+    h->tc = tc;
+    cudaStream_t s = h->stream;
+    tc->Kp = kp_for(h->d);
+    tc->BN = bn_for(tc->Kp);
+    tc->T = ceil_div(h->n, tc->BN);
+    tc->n_pad = tc->T * tc->BN;
+    const int Kp = tc->Kp;
+    STAG_CUDA_TRY(cudaMalloc(&tc->b_hi, tc->n_pad * Kp * sizeof(__half)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->b_lo, tc->n_pad * Kp * sizeof(__half)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->ccol, tc->n_pad * sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->cent, tc->T * Kp * sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->cg, Kp * sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->tsum, tc->T * Kp * sizeof(double)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->vmax_bits, sizeof(unsigned)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->qmax_bits, sizeof(unsigned)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->kk, sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->err, sizeof(int)));
+    STAG_CUDA_TRY(cudaMallocHost(&tc->err_host, sizeof(int)));
+    STAG_CUDA_TRY(cudaMemsetAsync(tc->err, 0, sizeof(int), s));
+    STAG_CUDA_TRY(cudaMemsetAsync(tc->vmax_bits, 0, sizeof(unsigned), s));
+
+    count_launch(5);
+    tc_centres_kernel<<<(unsigned)tc->T, 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->tsum, tc->cent);
+    tc_global_centre_kernel<<<1, 128, 0, s>>>(tc->tsum, tc->T, Kp, h->n, h->d, tc->cg);
+    tc_vmax_kernel<<<grid_for(h->n * h->d, 256), 256, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->vmax_bits);
+    const double c = h->a * 1.4426950408889634;
+    tc_split_points_kernel<<<grid_for(tc->n_pad, 128), 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->n_pad, tc->cent,
+                                                                    tc->cg, tc->vmax_bits, c, tc->b_hi, tc->b_lo,
+                                                                    tc->ccol);
+    STAG_CUDA_TRY(cudaGetLastError());
+    int rc = make_map(&tc->map_bhi, tc->b_hi, tc->n_pad, Kp, tc->BN);
+    if (!rc) rc = make_map(&tc->map_blo, tc->b_lo, tc->n_pad, Kp, tc->BN);
+    return rc;
+}
+
+static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
+    TcData *tc = h->tc;
+    const int Kp = tc->Kp;
+    if (tc->a_rows_cap < m_pad) {
+        cudaFree(tc->a_hi);
+        cudaFree(tc->a_lo);
+        tc->a_hi = tc->a_lo = nullptr;
+        tc->a_rows_cap = 0;
+        STAG_CUDA_TRY(cudaMalloc(&tc->a_hi, m_pad * Kp * sizeof(__half)));
+        STAG_CUDA_TRY(cudaMalloc(&tc->a_lo, m_pad * Kp * sizeof(__half)));
+        tc->a_rows_cap = m_pad;
+        int rc = make_map(&tc->map_ahi, tc->a_hi, m_pad, Kp, BM);
+        if (!rc) rc = make_map(&tc->map_alo, tc->a_lo, m_pad, Kp, BM);
+        if (rc) return rc;
+    }
+    const int64_t need = tc->T * m_pad;
+    if (tc->rt_cap < need) {
+        cudaFree(tc->rowterm);
+        tc->rowterm = nullptr;
+        tc->rt_cap = 0;
+        STAG_CUDA_TRY(cudaMalloc(&tc->rowterm, need * sizeof(float)));
+        tc->rt_cap = need;
+    }
+    return 0;
+}
+
+int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag) {
+    TcData *tc = h->tc;
+    const int Kp = tc->Kp;
+    const int64_t m_pad = round_up(m, BM);
+    int rc = ensure_query_scratch(h, m_pad);
+    if (rc) return rc;
+    if (dflag) {
+        rc = launch_check_finite_f32(dQ, m * h->d, dflag, s);
+        if (rc) return rc;
+    }
+    const double c = h->a * 1.4426950408889634;
+    STAG_CUDA_TRY(cudaMemsetAsync(tc->qmax_bits, 0, sizeof(unsigned), s));
+    count_launch(3);
+    tc_qmax_kernel<<<grid_for(m * h->d, 256), 256, 0, s>>>(dQ, m, h->d, tc->cg, tc->qmax_bits);
+    tc_split_queries_kernel<<<grid_for(m_pad * Kp, 256), 256, 0, s>>>(dQ, m, h->d, Kp, m_pad, tc->cg, tc->qmax_bits,
+                                                                      tc->vmax_bits, c, tc->a_hi, tc->a_lo, tc->kk);
+    {
+        const int tpb = 64;
+        static std::once_flag attr_once;
+        std::call_once(attr_once, []() {
+            cudaFuncSetAttribute(tc_rowterm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4);
+        });
+        dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
+        tc_rowterm_kernel<<<grid, 128, Kp * 128 * sizeof(float), s>>>(dQ, m, h->d, Kp, m_pad, tc->cent, tc->T, tpb,
+                                                                      (float)c, tc->rowterm);
+    }
+    STAG_CUDA_TRY(cudaGetLastError());
+
+    // work units: (query tile, range of point tiles), enough for ~8 per SM
+    const int64_t q_tiles = m_pad / BM;
+    int64_t splits = std::max<int64_t>(1, ceil_div((int64_t)h->sm_count * 8, q_tiles));
+    splits = std::min<int64_t>(splits, std::max<int64_t>(1, tc->T / 4));
+    const int64_t tps = ceil_div(tc->T, splits);
+    splits = ceil_div(tc->T, tps);
+    rc = ensure_partials(h, splits * m);
+    if (rc) return rc;
+    TcParams prm;
+    prm.ccol = tc->ccol;
+    prm.rowterm = tc->rowterm;
+    prm.kk = tc->kk;
+    prm.part_sum = h->part.sum;
+    prm.part_shift = h->part.shift;
+    prm.err = tc->err;
+    prm.m = m;
+    prm.m_pad = m_pad;
+    prm.T = tc->T;
+    prm.q_tiles = q_tiles;
+    prm.tiles_per_split = tps;
+    prm.units = q_tiles * splits;
+    switch (Kp) {
+        case 16: rc = launch_tc<16, 256, 4, 8, 2>(h, prm, s); break;
+        case 32: rc = launch_tc<32, 256, 4, 8, 2>(h, prm, s); break;
+        case 64: rc = launch_tc<64, 256, 2, 8, 2>(h, prm, s); break;
+        case 128: rc = launch_tc<128, 128, 2, 8, 1>(h, prm, s); break;
+        default: return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported d");
+    }
+    if (rc) return rc;
+    return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0, dOut,
+                          s);
+}
+
+int tc_check_error(stag_kde *h, cudaStream_t s) {
+    TcData *tc = h->tc;
+    if (!tc) return 0;
+    STAG_CUDA_TRY(cudaMemcpyAsync(tc->err_host, tc->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*tc->err_host) {
+        STAG_CUDA_TRY(cudaMemsetAsync(tc->err, 0, sizeof(int), s));
+        return fail(STAG_KDE_ETIMEDOUT, "tensor-core kernel: a bounded wait expired");
+    }
+    return 0;
+}
 
 }  // namespace stagkde
