@@ -111,7 +111,11 @@ int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStre
 int launch_combine(const double *part_sum, const float *part_shift, int64_t m, int splits,
                    double scale, double *out, cudaStream_t s);
 
+// kd_order.cu
+int kd_reorder(const float *dX, int64_t n, int64_t d, int BN, float *dXs, cudaStream_t s);
+
 // kde_tc.cu
+int tc_tile_points(int64_t d);
 int tc_prepare_points(stag_kde *h, const float *dX);
 int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag);
 void tc_free(stag_kde *h);

@@ -712,6 +712,8 @@ int launch_tc(stag_kde *h, const TcParams &prm, cudaStream_t s) {
 
 bool tc_supported(int64_t d) { return kp_for(d) != 0; }
 
+int tc_tile_points(int64_t d) { return kp_for(d) ? bn_for(kp_for(d)) : 0; }
+
 void tc_free(stag_kde *h) {
     TcData *tc = h->tc;
     if (!tc) return;

@@ -243,7 +243,18 @@ stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, d
         // the plain form's layout is always built: it is also the fallback and the
         // reference used by the tensor-core form's tests
         rc = simt_prepare_points(h, dX);
-        if (!rc && form == STAG_KDE_FORM_TC) rc = tc_prepare_points(h, dX);
+        if (!rc && form == STAG_KDE_FORM_TC) {
+            // tensor-core form: tiles of spatially coherent points (k-d order)
+            float *dXs = nullptr;
+            if ((e = cudaMalloc(&dXs, bytes)) != cudaSuccess) {
+                rc = cuda_fail(e, "cudaMalloc(ordered X)");
+            } else {
+                rc = kd_reorder(dX, n, d, tc_tile_points(d), dXs, h->stream);
+                if (!rc) rc = tc_prepare_points(h, dXs);
+                cudaStreamSynchronize(h->stream);
+                cudaFree(dXs);
+            }
+        }
         cudaStreamSynchronize(h->stream);
         cudaFree(dX);
         if (rc) return bail("prepare", cudaSuccess);
