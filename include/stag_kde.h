@@ -64,7 +64,10 @@ typedef struct stag_kde_opts {
     int form;       /* STAG_KDE_FORM_*; 0 = AUTO                                    */
     int normalise;  /* 1: return (1/n) * sum (the paper's K(q)); 0: the plain sum     */
     int device;     /* CUDA device ordinal; -1 = the calling thread's current device  */
-    int reserved[5];/* must be zero                                                   */
+    int tc_no_check;/* tensor-core form only. 0 (default): every query gets an error   *
+                     * estimate; those above 7.5e-5 relative are recomputed with the    *
+                     * plain FP32 form. 1: skip the estimate and keep every result.     */
+    int reserved[4];/* must be zero                                                   */
 } stag_kde_opts;
 
 /* Fills *o with the defaults (AUTO form, unnormalised, current device). */
@@ -110,6 +113,11 @@ int stag_kde_reserve(stag_kde_t *h, int64_t m);
 /* Reads back the handle's parameters; any pointer may be NULL. `form` is the form the
  * handle evaluates with (AUTO resolved). */
 int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *dtype, int *form);
+
+/* Number of queries of the handle's most recent query call that the tensor-core
+ * form's error estimate handed to the plain FP32 form (0 for other forms).
+ * Synchronises with the device. */
+int stag_kde_last_recomputed(stag_kde_t *h, int64_t *count);
 
 /* Releases the handle and its device memory. NULL-safe. */
 void stag_kde_destroy(stag_kde_t *h);

@@ -30,7 +30,7 @@ class StagKdeError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("normalise", ctypes.c_int), ("device", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("tc_no_check", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 # (name, restype, argtypes) for every entry point declared in include/stag_kde.h
@@ -45,6 +45,7 @@ SIGNATURES = [
     ("stag_kde_info", _INT, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_DBL),
                              ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     ("stag_kde_destroy", None, [_VP]),
+    ("stag_kde_last_recomputed", _INT, [_VP, ctypes.POINTER(_I64)]),
     ("stag_kde_last_error", ctypes.c_char_p, []),
     ("stag_kde_version", ctypes.c_char_p, []),
     ("stag_kde_launch_count", ctypes.c_uint64, []),

@@ -57,6 +57,7 @@ struct stag_kde {
     int dtype = STAG_KDE_F32;
     int form = STAG_KDE_FORM_SIMT_F32;
     int normalise = 0;
+    bool tc_check = true;  // recompute queries the tensor-core error estimate flags
     cudaStream_t stream = nullptr;  // the handle's own stream (host API)
 
     // plain FP32 form: tile-transposed points
@@ -103,6 +104,10 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
 int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaStream_t s,
                    int *dflag);
 int ensure_partials(stag_kde *h, int64_t entries);
+// Recomputes with the plain FP32 form the rows idx[0 .. *count) of dQ (device count)
+// and writes their densities to dOut[idx[j]].
+int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
+                    cudaStream_t s);
 int ensure_qt(stag_kde *h, int64_t floats);
 int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s);
 int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s);
@@ -120,6 +125,7 @@ int tc_prepare_points(stag_kde *h, const float *dX);
 int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag);
 void tc_free(stag_kde *h);
 int tc_check_error(stag_kde *h, cudaStream_t s);
+int tc_fixed_rows(stag_kde *h, int64_t *count);
 bool tc_supported(int64_t d);
 
 }  // namespace stagkde

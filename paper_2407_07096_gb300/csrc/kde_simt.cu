@@ -103,7 +103,11 @@ __global__ void __launch_bounds__(256, 2)
 kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles,
                     const float *__restrict__ qt, int64_t m, int d_pad, float negc,
                     int64_t tiles_per_split, double *__restrict__ part_sum,
-                    float *__restrict__ part_shift) {
+                    float *__restrict__ part_shift, const int *__restrict__ count) {
+    // `count` (optional, device memory): only the first *count query rows are real;
+    // blocks past them exit at once (the partials keep the row stride m)
+    const int64_t m_real = count ? (int64_t)*count : m;
+    if ((int64_t)blockIdx.x * kSimtTile >= m_real) return;
     __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
     __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
 
@@ -219,7 +223,7 @@ kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles,
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int64_t q = qtile * kSimtTile + ty * 4 + i;
-            if (q < m) {
+            if (q < m_real) {
                 part_sum[(int64_t)split * m + q] = row[i].acc64;
                 part_shift[(int64_t)split * m + q] = row[i].shift;
             }
@@ -283,6 +287,37 @@ kde_simt_f64_kernel(const double *__restrict__ X, int64_t n, const double *__res
         }
     }
     if (j < m) out[j] = s;
+}
+
+// Rows idx[0 .. *count) of the row-major Q, in that order, into the tile-transposed
+// layout (rows past *count are zero).
+__global__ void gather_rows_tiles_kernel(const float *__restrict__ Q, int64_t d, int d_pad,
+                                         const int *__restrict__ idx, const int *__restrict__ count, int64_t m_cap,
+                                         float *__restrict__ qt) {
+    const int64_t cnt = *count;
+    const int64_t total = ((min(cnt, m_cap) + kSimtTile - 1) / kSimtTile) * d_pad * kSimtTile;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e % kSimtTile);
+        const int64_t rest = e / kSimtTile;
+        const int k = (int)(rest % d_pad);
+        const int64_t j = (rest / d_pad) * kSimtTile + r;
+        qt[e] = (j < cnt && k < d) ? Q[(int64_t)idx[j] * d + k] : 0.f;
+    }
+}
+
+// out[idx[j]] = sum over splits of part_sum * 2^part_shift (FP64, split order), j < *count.
+__global__ void combine_scatter_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
+                                       int64_t m_stride, int splits, const int *__restrict__ idx,
+                                       const int *__restrict__ count, double scale, double *__restrict__ out) {
+    const int64_t cnt = *count;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+        float smax = -INFINITY;
+        for (int k = 0; k < splits; ++k) smax = fmaxf(smax, part_shift[(int64_t)k * m_stride + j]);
+        double tot = 0.0;
+        for (int k = 0; k < splits; ++k)
+            tot += ldexp(part_sum[(int64_t)k * m_stride + j], clamp_exp(part_shift[(int64_t)k * m_stride + j] - smax));
+        out[idx[j]] = ldexp(tot, clamp_exp(smax)) * scale;
+    }
 }
 
 int grid_for(int64_t total, int threads) {
@@ -374,14 +409,42 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
     prof_start(h, s);
     if (h->d_pad <= kSimtKC)
         kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
-                                                      tps, h->part.sum, h->part.shift);
+                                                      tps, h->part.sum, h->part.shift, nullptr);
     else
         kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
-                                                       tps, h->part.sum, h->part.shift);
+                                                       tps, h->part.sum, h->part.shift, nullptr);
     prof_stop(h, s, (double)m * (double)h->n);
     STAG_CUDA_TRY(cudaGetLastError());
     return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
                           dOut, s);
+}
+
+int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
+                    cudaStream_t s) {
+    // the row set is only known on the device: size everything for all m rows and let
+    // the kernels skip what lies past *count
+    const int64_t q_tiles = ceil_div(m, kSimtTile);
+    int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
+    if (rc) return rc;
+    const int64_t tps = choose_tiles_per_split(h, q_tiles);
+    const int64_t splits = ceil_div(h->n_tiles, tps);
+    rc = ensure_partials(h, splits * m);
+    if (rc) return rc;
+    count_launch(3);
+    gather_rows_tiles_kernel<<<grid_for(q_tiles * h->d_pad * kSimtTile, 256), 256, 0, s>>>(dQ, h->d, h->d_pad, idx,
+                                                                                           count, m, h->qt);
+    const float negc = (float)(-h->a * 1.4426950408889634);
+    dim3 grid((unsigned)q_tiles, (unsigned)splits);
+    if (h->d_pad <= kSimtKC)
+        kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
+                                                      h->part.sum, h->part.shift, count);
+    else
+        kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
+                                                       h->part.sum, h->part.shift, count);
+    combine_scatter_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
+        h->part.sum, h->part.shift, m, (int)splits, idx, count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
 }
 
 int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag) {

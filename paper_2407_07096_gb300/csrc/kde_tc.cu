@@ -52,7 +52,8 @@ struct TcData {
     int64_t T = 0;       // number of point tiles
     int64_t n_pad = 0;   // T * BN
     __half *b_hi = nullptr, *b_lo = nullptr;  // [n_pad][Kp]
-    float *ccol = nullptr;                    // [T][BN]: c * C(x); +inf for padding points
+    float *ccol = nullptr;                    // [T][BN + 4]: c * C(x) (+inf for padding points), then
+                                              // the tile's RMS radius and 3 zeros
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
     float *cg = nullptr;                      // [Kp]: global centre c_g
     double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
@@ -67,6 +68,13 @@ struct TcData {
     int64_t rt_cap = 0;        // floats
     unsigned *qmax_bits = nullptr;  // max |u| over the batch (float bits)
     float *kk = nullptr;            // [1]: 2c / (scale_u scale_v)
+    float *unorm = nullptr;         // [m_cap]: ||q - c_g|| per query
+    int64_t unorm_cap = 0;
+    double *part_w = nullptr;       // [splits][m]: contribution-weighted tile radius sums
+    int64_t part_w_cap = 0;
+    int *fix_idx = nullptr;         // [m_cap]: queries handed to the plain form
+    int *fix_count = nullptr;       // device counter
+    int64_t fix_cap = 0;
     int *err = nullptr;             // device error code (timeouts)
     int *err_host = nullptr;        // pinned mirror
 };
@@ -78,6 +86,10 @@ constexpr int kErrTimeout = 1;
 constexpr float kShiftFloor = -0x1p100f;
 constexpr float kGuard = 0x1p64f;
 constexpr int BM = 128;  // queries per tile (MMA M, TMEM lanes)
+// Queries whose estimated tensor-core error exceeds this are recomputed with the plain
+// FP32 form; the estimate bounds the measured error from above (ratio <= ~0.96), so the
+// queries kept stay below ~7.2e-5 against the 1e-4 tolerance.
+constexpr double kTcErrThreshold = 7.5e-5;
 
 // ------------------------------------------------------------------ layout helpers
 template <int KP>
@@ -99,12 +111,12 @@ struct Cfg {
     static constexpr int B_PLANE = BN * KP * 2;
     static constexpr int A_BYTES = 2 * A_PLANE;
     static constexpr int B_BYTES = 2 * B_PLANE;
-    static constexpr int META_BYTES = BN * 4 + BM * 4;
+    static constexpr int META_BYTES = (BN + 4) * 4 + BM * 4;
     static constexpr int OFF_A = 0;
     static constexpr int OFF_B = OFF_A + AB * A_BYTES;
     static constexpr int OFF_META = OFF_B + SB * B_BYTES;
     static constexpr int OFF_MERGE = OFF_META + SMETA * META_BYTES;
-    static constexpr int OFF_BAR = OFF_MERGE + BM * 16;
+    static constexpr int OFF_BAR = OFF_MERGE + BM * 24;
     static constexpr int NBAR = 2 * SB + 2 * SMETA + 2 * AB + 4 + 3;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int BYTES = OFF_MISC + 64;
@@ -119,6 +131,7 @@ struct TcParams {
     const float *kk;       // device scalar
     double *part_sum;
     float *part_shift;
+    double *part_w;
     int *err;
     int64_t m, m_pad, T, q_tiles, tiles_per_split, units;
 };
@@ -153,15 +166,18 @@ struct RowState {
     float shift;
     float acc32;
     double acc64;
+    float w32;   // sum over chunks of (chunk sum) * (tile RMS radius), same units as acc
+    double w64;
 };
 
 // Sum of 2^(kk*D[j] - E - s - col[j]) over 32 columns, rescaling the row if needed.
+// Two independent packed accumulators keep the dependency chains short.
 __device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32], const float *__restrict__ col,
-                                          float kk, float E) {
+                                          float kk, float E, float vrad) {
     const uint64_t kk2 = pack2(kk, kk);
     float nb = -(E + st.shift);
-    uint64_t nb2 = pack2(nb, nb);
-    uint64_t acc2 = 0;  // {0.f, 0.f}
+    const uint64_t nb2 = pack2(nb, nb);
+    uint64_t acc_a = 0, acc_b = 0;  // {0.f, 0.f}
 #pragma unroll
     for (int j = 0; j < 32; j += 4) {
         const float4 c4 = *reinterpret_cast<const float4 *>(col + j);
@@ -172,12 +188,13 @@ __device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32],
         float a0, a1, a2, a3;
         unpack2(x01, a0, a1);
         unpack2(x23, a2, a3);
-        acc2 = add2(acc2, pack2(ptx::ex2_approx(a0), ptx::ex2_approx(a1)));
-        acc2 = add2(acc2, pack2(ptx::ex2_approx(a2), ptx::ex2_approx(a3)));
+        acc_a = add2(acc_a, pack2(ptx::ex2_approx(a0), ptx::ex2_approx(a1)));
+        acc_b = add2(acc_b, pack2(ptx::ex2_approx(a2), ptx::ex2_approx(a3)));
     }
-    float s0, s1;
-    unpack2(acc2, s0, s1);
-    float cs = s0 + s1;
+    float s0, s1, s2, s3;
+    unpack2(acc_a, s0, s1);
+    unpack2(acc_b, s2, s3);
+    float cs = (s0 + s1) + (s2 + s3);
     if (!(cs <= kGuard)) {
         // rare: first tile of a row, or a tile whose terms exceed the current shift by 2^64
         float mx = -INFINITY;
@@ -188,6 +205,8 @@ __device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32],
             const int de = cexp(st.shift - s_new);
             st.acc32 = ldexpf(st.acc32, de);
             st.acc64 = ldexp(st.acc64, de);
+            st.w32 = ldexpf(st.w32, de);
+            st.w64 = ldexp(st.w64, de);
             st.shift = s_new;
         }
         nb = -(E + st.shift);
@@ -196,6 +215,7 @@ __device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32],
         for (int j = 0; j < 32; ++j) cs += ptx::ex2_approx(fmaf(kk, __uint_as_float(D[j]), nb - col[j]));
     }
     st.acc32 += cs;
+    st.w32 = fmaf(cs, vrad, st.w32);
 }
 
 template <int KP, int BN, int SB, int SMETA, int AB>
@@ -318,8 +338,8 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     }
                     uint8_t *mbuf = smem + C::OFF_META + ms * C::META_BYTES;
                     ptx::mbar_arrive_expect_tx(&full_m[ms], C::META_BYTES);
-                    ptx::bulk_load(mbuf, p.ccol + t * BN, BN * 4, &full_m[ms]);
-                    ptx::bulk_load(mbuf + BN * 4, p.rowterm + t * p.m_pad + qt * BM, BM * 4, &full_m[ms]);
+                    ptx::bulk_load(mbuf, p.ccol + t * (BN + 4), (BN + 4) * 4, &full_m[ms]);
+                    ptx::bulk_load(mbuf + (BN + 4) * 4, p.rowterm + t * p.m_pad + qt * BM, BM * 4, &full_m[ms]);
                     ++issued_m;
                 }
             }
@@ -411,7 +431,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
             const int64_t split = u / p.q_tiles, qt = u % p.q_tiles;
             const int64_t t0 = split * p.tiles_per_split;
             const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
-            RowState st{kShiftFloor, 0.f, 0.0};
+            RowState st{kShiftFloor, 0.f, 0.0, 0.f, 0.0};
             for (int64_t t = t0; t < t1; ++t, ++tcount) {
                 const int acc = tcount & 1;
                 const int ms = tcount % SMETA;
@@ -426,35 +446,55 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                 }
                 ptx::tc_fence_after();
                 const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_BYTES);
-                const float E = meta[BN + row];
+                const float E = meta[BN + 4 + row];
+                const float vrad = meta[BN];
                 const float *col = meta + half * (BN / 2);
                 const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + half * (BN / 2);
                 constexpr int NCH = BN / 2 / 32;
+                // software pipeline: the TMEM load of chunk c+1 is in flight while chunk c
+                // is processed (tcgen05.wait::ld waits for every load issued before it)
+                uint32_t Da[32], Db[32];
+                ptx::tmem_ld_32x32b_x32(taddr, Da);
+                ptx::tmem_ld_wait();
+                ptx::reg_fence32(Da);
 #pragma unroll
-                for (int c = 0; c < NCH; c += 2) {
-                    uint32_t D0[32], D1[32];
-                    ptx::tmem_ld_32x32b_x32(taddr + c * 32, D0);
-                    if (c + 1 < NCH) ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, D1);
-                    ptx::tmem_ld_wait();
-                    if (c + 2 >= NCH) {
+                for (int c = 0; c < NCH; ++c) {
+                    if (c + 1 < NCH) {
+                        if (c & 1)
+                            ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Da);
+                        else
+                            ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Db);
+                    } else {
                         // every TMEM column of this buffer has been read: hand it back
                         ptx::tc_fence_before();
                         __syncwarp();
                         if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
                     }
-                    epi_chunk(st, D0, col + c * 32, kk, E);
-                    if (c + 1 < NCH) epi_chunk(st, D1, col + (c + 1) * 32, kk, E);
+                    if (c & 1)
+                        epi_chunk(st, Db, col + c * 32, kk, E, vrad);
+                    else
+                        epi_chunk(st, Da, col + c * 32, kk, E, vrad);
+                    if (c + 1 < NCH) {
+                        ptx::tmem_ld_wait();
+                        if (c & 1)
+                            ptx::reg_fence32(Da);
+                        else
+                            ptx::reg_fence32(Db);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&empty_m[ms]);
                 st.acc64 += (double)st.acc32;
                 st.acc32 = 0.f;
+                st.w64 += (double)st.w32;
+                st.w32 = 0.f;
             }
             if (!ok) break;
             // merge the two column halves of each row (half 1 hands its sums to half 0
             // through shared memory), then store the unit's partials
             double *msum = reinterpret_cast<double *>(merge);
-            float *mshift = merge + 2 * BM;
+            double *mw = msum + BM;
+            float *mshift = merge + 4 * BM;
             if (half == 1) {
                 const bool got = ptx::mbar_wait_bounded(merge_empty, (ucount & 1) ^ 1, kWaitLimitNs, abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
@@ -462,6 +502,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     break;
                 }
                 msum[row] = st.acc64;
+                mw[row] = st.w64;
                 mshift[row] = st.shift;
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(merge_full);
@@ -472,15 +513,19 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     break;
                 }
                 const double oa = msum[row];
+                const double ow = mw[row];
                 const float os = mshift[row];
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(merge_empty);
                 const float sm = fmaxf(st.shift, os);
-                const double tot = ldexp(st.acc64, cexp(st.shift - sm)) + ldexp(oa, cexp(os - sm));
+                const int e0 = cexp(st.shift - sm), e1 = cexp(os - sm);
+                const double tot = ldexp(st.acc64, e0) + ldexp(oa, e1);
+                const double wt = ldexp(st.w64, e0) + ldexp(ow, e1);
                 const int64_t q = qt * BM + row;
                 if (q < p.m) {
                     p.part_sum[split * p.m + q] = tot;
                     p.part_shift[split * p.m + q] = sm;
+                    p.part_w[split * p.m + q] = wt;
                 }
             }
             ++ucount;
@@ -571,7 +616,36 @@ __global__ void tc_split_points_kernel(const float *__restrict__ X, int64_t n, i
             bhi[i * Kp + k] = h;
             blo[i * Kp + k] = l;
         }
-        ccol[i] = i < n ? (float)(c * (nv2 + 2.0 * dv)) : INFINITY;
+        ccol[t * (BN + 4) + (i - t * BN)] = i < n ? (float)(c * (nv2 + 2.0 * dv)) : INFINITY;
+    }
+}
+
+// Per tile: the RMS distance of its points from the tile centre (used by the per-query
+// error estimate), stored after the tile's column terms.
+__global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
+                                      const float *__restrict__ cent, float *__restrict__ ccol) {
+    __shared__ double red[128];
+    const int64_t t = blockIdx.x;
+    const int64_t r0 = t * BN, cnt = min((int64_t)BN, n - r0);
+    double acc = 0.0;
+    for (int64_t r = threadIdx.x; r < cnt; r += blockDim.x) {
+        double s2 = 0.0;
+        for (int64_t k = 0; k < d; ++k) {
+            const double v = (double)X[(r0 + r) * d + k] - (double)cent[t * Kp + k];
+            s2 += v * v;
+        }
+        acc += s2;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 64; o; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) {
+        float v = 0.f;
+        if (threadIdx.x == 0 && cnt > 0) v = (float)sqrt(red[0] / (double)cnt);
+        ccol[t * (BN + 4) + BN + threadIdx.x] = v;
     }
 }
 
@@ -611,7 +685,8 @@ __global__ void tc_split_queries_kernel(const float *__restrict__ Q, int64_t m, 
 // One block per (128-query tile, group of point tiles); queries staged transposed.
 __global__ void __launch_bounds__(128)
 tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
-                  const float *__restrict__ cent, int64_t T, int tiles_per_block, float c, float *__restrict__ R) {
+                  const float *__restrict__ cent, int64_t T, int tiles_per_block, float c, float *__restrict__ R,
+                  const float *__restrict__ cg, float *__restrict__ unorm) {
     extern __shared__ float sq[];  // [Kp][128]
     const int64_t q0 = (int64_t)blockIdx.x * 128;
     const int r = threadIdx.x;
@@ -620,6 +695,14 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int
         sq[k * 128 + r] = (q < m && k < d) ? Q[q * d + k] : 0.f;
     }
     __syncthreads();
+    if (blockIdx.y == 0) {
+        float s = 0.f;
+        for (int k = 0; k < Kp; ++k) {
+            const float df = sq[k * 128 + r] - cg[k];
+            s = fmaf(df, df, s);
+        }
+        unorm[q0 + r] = q0 + r < m ? sqrtf(s) : 0.f;
+    }
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
     const bool real = q0 + r < m;
@@ -638,6 +721,30 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int
             s1 = fmaf(d3, d3, s1);
         }
         R[t * m_pad + q0 + r] = real ? c * (s0 + s1) : 0.f;
+    }
+}
+
+// FP64 combine of the per-split partials (as kde_combine.cu) plus the per-query error
+// estimate of the tensor-core form,
+//     est = 2^-21 * a * ||q - c_g|| * (sum_t S_t r_t) / (sum_t S_t),
+// S_t the query's sum over tile t and r_t that tile's RMS radius. Queries with
+// est > thr (or an empty sum) are appended to fix_idx for the plain FP32 form.
+__global__ void tc_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
+                                  const double *__restrict__ part_w, int64_t m, int splits, double scale,
+                                  const float *__restrict__ unorm, double a, double thr, double *__restrict__ out,
+                                  int *__restrict__ fix_idx, int *__restrict__ fix_count) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        float smax = -INFINITY;
+        for (int k = 0; k < splits; ++k) smax = fmaxf(smax, part_shift[(int64_t)k * m + j]);
+        double tot = 0.0, wt = 0.0;
+        for (int k = 0; k < splits; ++k) {
+            const int e = cexp(part_shift[(int64_t)k * m + j] - smax);
+            tot += ldexp(part_sum[(int64_t)k * m + j], e);
+            wt += ldexp(part_w[(int64_t)k * m + j], e);
+        }
+        out[j] = ldexp(tot, cexp(smax)) * scale;
+        const double est = tot > 0.0 ? 0x1p-21 * a * (double)unorm[j] * (wt / tot) : INFINITY;
+        if (est > thr && fix_idx) fix_idx[atomicAdd(fix_count, 1)] = (int)j;
     }
 }
 
@@ -730,6 +837,10 @@ void tc_free(stag_kde *h) {
     cudaFree(tc->qmax_bits);
     cudaFree(tc->kk);
     cudaFree(tc->err);
+    cudaFree(tc->unorm);
+    cudaFree(tc->part_w);
+    cudaFree(tc->fix_idx);
+    cudaFree(tc->fix_count);
     if (tc->err_host) cudaFreeHost(tc->err_host);
     delete tc;
     h->tc = nullptr;
@@ -747,7 +858,7 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     const int Kp = tc->Kp;
     STAG_CUDA_TRY(cudaMalloc(&tc->b_hi, tc->n_pad * Kp * sizeof(__half)));
     STAG_CUDA_TRY(cudaMalloc(&tc->b_lo, tc->n_pad * Kp * sizeof(__half)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->ccol, tc->n_pad * sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->ccol, tc->T * (tc->BN + 4) * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->cent, tc->T * Kp * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->cg, Kp * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->tsum, tc->T * Kp * sizeof(double)));
@@ -767,6 +878,8 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     tc_split_points_kernel<<<grid_for(tc->n_pad, 128), 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->n_pad, tc->cent,
                                                                     tc->cg, tc->vmax_bits, c, tc->b_hi, tc->b_lo,
                                                                     tc->ccol);
+    count_launch();
+    tc_tile_radius_kernel<<<(unsigned)tc->T, 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->ccol);
     STAG_CUDA_TRY(cudaGetLastError());
     int rc = make_map(&tc->map_bhi, tc->b_hi, tc->n_pad, Kp, tc->BN);
     if (!rc) rc = make_map(&tc->map_blo, tc->b_lo, tc->n_pad, Kp, tc->BN);
@@ -788,6 +901,17 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         if (!rc) rc = make_map(&tc->map_alo, tc->a_lo, m_pad, Kp, BM);
         if (rc) return rc;
     }
+    if (tc->unorm_cap < m_pad) {
+        cudaFree(tc->unorm);
+        cudaFree(tc->fix_idx);
+        tc->unorm = nullptr;
+        tc->fix_idx = nullptr;
+        tc->unorm_cap = 0;
+        STAG_CUDA_TRY(cudaMalloc(&tc->unorm, m_pad * sizeof(float)));
+        STAG_CUDA_TRY(cudaMalloc(&tc->fix_idx, m_pad * sizeof(int)));
+        tc->unorm_cap = m_pad;
+    }
+    if (!tc->fix_count) STAG_CUDA_TRY(cudaMalloc(&tc->fix_count, sizeof(int)));
     const int64_t need = tc->T * m_pad;
     if (tc->rt_cap < need) {
         cudaFree(tc->rowterm);
@@ -823,7 +947,7 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
         });
         dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
         tc_rowterm_kernel<<<grid, 128, Kp * 128 * sizeof(float), s>>>(dQ, m, h->d, Kp, m_pad, tc->cent, tc->T, tpb,
-                                                                      (float)c, tc->rowterm);
+                                                                      (float)c, tc->rowterm, tc->cg, tc->unorm);
     }
     STAG_CUDA_TRY(cudaGetLastError());
 
@@ -835,12 +959,20 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
     splits = ceil_div(tc->T, tps);
     rc = ensure_partials(h, splits * m);
     if (rc) return rc;
+    if (tc->part_w_cap < splits * m) {
+        cudaFree(tc->part_w);
+        tc->part_w = nullptr;
+        tc->part_w_cap = 0;
+        STAG_CUDA_TRY(cudaMalloc(&tc->part_w, splits * m * sizeof(double)));
+        tc->part_w_cap = splits * m;
+    }
     TcParams prm;
     prm.ccol = tc->ccol;
     prm.rowterm = tc->rowterm;
     prm.kk = tc->kk;
     prm.part_sum = h->part.sum;
     prm.part_shift = h->part.shift;
+    prm.part_w = tc->part_w;
     prm.err = tc->err;
     prm.m = m;
     prm.m_pad = m_pad;
@@ -856,8 +988,24 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
         default: return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported d");
     }
     if (rc) return rc;
-    return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0, dOut,
-                          s);
+    const bool check = h->tc_check;
+    if (check) STAG_CUDA_TRY(cudaMemsetAsync(tc->fix_count, 0, sizeof(int), s));
+    count_launch();
+    tc_combine_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
+        h->part.sum, h->part.shift, tc->part_w, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0, tc->unorm,
+        h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
+    STAG_CUDA_TRY(cudaGetLastError());
+    if (!check) return 0;
+    // queries whose estimated error is above the threshold: plain FP32 form
+    return simt_fixup_rows(h, dQ, m, tc->fix_idx, tc->fix_count, dOut, s);
+}
+
+int tc_fixed_rows(stag_kde *h, int64_t *count) {
+    TcData *tc = h->tc;
+    int v = 0;
+    if (tc && tc->fix_count && h->tc_check) STAG_CUDA_TRY(cudaMemcpy(&v, tc->fix_count, sizeof(int), cudaMemcpyDeviceToHost));
+    *count = v;
+    return 0;
 }
 
 int tc_check_error(stag_kde *h, cudaStream_t s) {

@@ -213,6 +213,7 @@ stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, d
     h->dtype = dtype;
     h->form = form;
     h->normalise = o.normalise ? 1 : 0;
+    h->tc_check = o.tc_no_check == 0;
     auto bail = [&](const char *what, cudaError_t e) -> stag_kde_t * {
         if (e != cudaSuccess) cuda_fail(e, what);
         free_handle(h);
@@ -333,6 +334,14 @@ int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *d
 }
 
 void stag_kde_destroy(stag_kde_t *h) { free_handle(h); }
+
+int stag_kde_last_recomputed(stag_kde_t *h, int64_t *count) {
+    if (!h || !count) return fail(STAG_KDE_EINVAL, "handle or count is NULL");
+    *count = 0;
+    if (h->form != STAG_KDE_FORM_TC) return 0;
+    DeviceGuard g(h->device);
+    return tc_fixed_rows(h, count);
+}
 
 int stag_kde_profile_begin(stag_kde_t *h) {
     if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");

@@ -27,7 +27,7 @@ class ExactGaussianKDE:
     """Exact Gaussian kernel density over a point set resident on one GPU."""
 
     def __init__(self, X, a: float, form: str = "auto", normalise: bool = False,
-                 device: int | None = None, dtype=None):
+                 device: int | None = None, dtype=None, tc_check: bool = True):
         lib = L.load()
         try:
             import torch
@@ -46,6 +46,7 @@ class ExactGaussianKDE:
         opts.form = L.FORMS[form]
         opts.normalise = 1 if normalise else 0
         opts.device = -1 if device is None else int(device)
+        opts.tc_no_check = 0 if tc_check else 1
         h = lib.stag_kde_create_ex(Xh.ctypes.data, self._dt, Xh.shape[0], Xh.shape[1], float(a),
                                    ctypes.byref(opts))
         if not h:
@@ -89,6 +90,12 @@ class ExactGaussianKDE:
         L.check(self._lib.stag_kde_query_dev(self._h, Q.data_ptr(), m, out.data_ptr(),
                                              ctypes.c_void_p(s.cuda_stream)))
         return out
+
+    def last_recomputed(self) -> int:
+        """Queries of the last call that the tensor-core error estimate sent to FP32."""
+        c = ctypes.c_int64()
+        L.check(self._lib.stag_kde_last_recomputed(self._h, ctypes.byref(c)))
+        return c.value
 
     def profile_begin(self):
         L.check(self._lib.stag_kde_profile_begin(self._h))

@@ -2,9 +2,10 @@
 
 Tolerance: 1e-4 relative per query (the stated bar of the split-precision form). The
 form's error grows with a * ||u|| * ||v|| (query distance from the data mean times tile
-radius, see kde_tc.cu); the cases here stay in the regime the library's AUTO selection
-hands to this form, and the ill-conditioned regime is checked against the error model.
-Sizes span several 128-query and 256-point tiles with ragged tails."""
+radius, see kde_tc.cu). Every query gets an error estimate; those above 7.5e-5 are
+recomputed with the plain FP32 form, so the bar holds in every regime. Tests with the
+check switched off measure the tensor-core arithmetic alone where it is well inside the
+bar. Sizes span several 128-query and 256-point tiles with ragged tails."""
 import math
 
 import numpy as np
@@ -26,8 +27,8 @@ def K():
     return ExactGaussianKDE
 
 
-def check_tc(K, X, Q, a, tol=TOL):
-    with K(X, a, form="tc") as kde:
+def check_tc(K, X, Q, a, tol=TOL, tc_check=True):
+    with K(X, a, form="tc", tc_check=tc_check) as kde:
         assert kde.form == "tc"
         got = kde.query(Q)
     ref = oracle.kde(X, Q, a)
@@ -52,6 +53,27 @@ def test_tc_ragged_sizes(K, n, m):
 def test_tc_bandwidths(K, a):
     X, Q = mixture_inputs(11, 6000, 400, 8, spread=4.0)
     check_tc(K, X, Q, a)
+
+
+@pytest.mark.parametrize("d,a", [(8, 0.5), (16, 0.3), (64, 0.02)])
+def test_tc_arithmetic_alone_without_recompute(K, d, a):
+    # the tensor-core results themselves, no FP32 recompute of any query
+    X, Q = mixture_inputs(40 + d, 6000, 500, d, spread=4.0)
+    check_tc(K, X, Q, a, tc_check=False)
+
+
+def test_tc_ill_conditioned_queries_are_recomputed(K):
+    # d = 128, a = 1: the exponent's condition number is ~150, far outside what split
+    # FP16 products can carry; the estimate must hand those queries to the FP32 form
+    X, Q = mixture_inputs(13, 4000, 300, 128, k=4, spread=3.0)
+    with K(X, 1.0, form="tc") as kde:
+        got = kde.query(Q)
+        redo = kde.last_recomputed()
+    ref = oracle.kde(X, Q, 1.0)
+    _, _, kappa = oracle.kde_log(X, Q, 1.0)
+    from tests._common import tol_f32
+    assert redo > 0.9 * len(Q)
+    assert np.all(oracle.rel_err(got, ref) <= np.maximum(TOL, tol_f32(kappa, 128)))
 
 
 def test_tc_a_zero_is_exactly_n(K):
@@ -123,8 +145,10 @@ def test_tc_single_instance_d16_workload_sampled(K):
     for a in (0.01, 0.1, 1.0):
         with K(X, a, form="tc") as kde:
             got = kde.query(Q)
+            redo = kde.last_recomputed()
         ref = oracle.kde(X, Q[idx], a)
         assert oracle.rel_err(got[idx], ref).max() <= TOL, a
+        assert redo <= 0.1 * len(Q), (a, redo)
 
 
 @pytest.mark.slow
