@@ -65,7 +65,7 @@ def load(path: str | None = None):
     with _lock:
         if _lib is not None and path is None:
             return _lib
-        p = path or _build.LIB
+        p = path or os.environ.get("STAG_KDE_LIB") or _build.LIB
         if not os.path.exists(p):
             raise RuntimeError(f"CUDA library not built ({p} missing): run __graft_entry__.build() "
                                "or python -m paper_2407_07096_gb300.build")

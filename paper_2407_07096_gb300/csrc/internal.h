@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/stag_kde.h"
+#include "stag_kde.h"
 
 namespace stagkde {
 

@@ -2,38 +2,46 @@
 // sm_103a: tcgen05.mma into TMEM, operands fed by TMA, exp and row sum fused into the
 // epilogue, so the m x n matrix of kernel values never exists in memory.
 //
-// Arithmetic. The point set is cut into tiles of BN points; tile t has a centre c_t
-// (the FP64 mean of its points, stored as FP32) and the queries are centred on the
-// global mean c_g. With v = x - c_t, u = q - c_g and D_t = c_t - c_g,
+// Arithmetic. The point set is cut into tiles of BN points (spatially coherent, k-d
+// order); tile t has a centre c_t (the FP64 mean of its points, stored as FP32) and the
+// queries are centred on the global mean c_g. With v = x - c_t, u = q - c_g and
+// D_t = c_t - c_g,
 //     ||q - x||^2 = ||q - c_t||^2 + ( ||v||^2 + 2 D_t . v ) - 2 u . v        (exact)
-//                 = R(q, t)       +   C(x)                   - 2 u . v
+//                 =  R(q, t)     +        g(x)             - 2 u . v
 // R is computed by direct differences in FP32 (rowterm kernel, one value per query and
-// tile), C in FP64 at create time (one value per point), and u . v on the tensor cores
+// tile), g in FP64 at create time (one value per point), and u . v on the tensor cores
 // with FP16 hi/lo splits of u and v (power-of-two scaled into FP16 range):
 //     u . v ~ u_hi . v_hi + u_hi . v_lo + u_lo . v_hi        (three MMAs, FP32 accumulate)
 // which represents both operands to ~2^-22 and drops only the u_lo . v_lo term (~2^-22).
-// The cancellation of the expansion is confined to the size of ||v|| (the tile radius)
-// and ||u||; the epilogue evaluates, per pair,
-//     e = 2^( kk * D - (c R + s_row) - c C ),   c = a log2(e), kk = 2c / (scale_u scale_v)
+// The point term g rides along as a fourth MMA of K = 16: the A side is the constant
+// column [s_a, s_a, s_a, 0, ...] and the B side holds -g / (2 scale) split into three
+// FP16 pieces (~2^-33), so the accumulator already holds u.v - g/2 in scaled units and
+// the epilogue needs no per-column data. Per pair it evaluates
+//     e = 2^( kk * D - (c R + s_row) ),   c = a log2(e), kk = 2c / (scale_u scale_v)
 // with the same integer per-row shift s as the plain form (see kde_simt.cu) so that
 // rows whose every term is below FP32's range are still represented.
 //
 // Kernel structure (persistent, one CTA per SM, warp-specialised):
-//   warp 0      TMA producer: per work unit the query tile's A planes (u_hi, u_lo), per
-//               point tile the B planes (v_hi, v_lo) and a metadata block (C of the
-//               tile's points, R of the unit's 128 queries) into rings of stages;
-//   warp 1      allocates TMEM; one thread issues 3 * K/16 MMAs per tile into one of
+//   warp 0      TMA producer: per work unit the query tile's A planes (u_hi, u_lo, the
+//               constant column), per point tile the B planes (v_hi, v_lo, -g pieces)
+//               and a metadata block (R of the unit's 128 queries, the tile's RMS
+//               radius) into rings of stages;
+//   warp 1      allocates TMEM; one thread issues 3 * K/16 + 1 MMAs per tile into one of
 //               two TMEM accumulators (128 lanes x BN columns, FP32) and commits;
-//   warps 2..9  epilogue: each thread owns one query row (its TMEM lane) and half of the
-//               tile's columns: tcgen05.ld, two packed FP32 ops, ex2, packed add.
+//   4*EG warps  epilogue: each thread owns one query row (its TMEM lane) and BN/EG of
+//               the tile's columns: tcgen05.ld, packed FMA, ex2, packed add.
 // A work unit is (query tile of 128 rows, contiguous range of point tiles); the partial
-// sums per (range, query) are combined in FP64 by kde_combine.cu.
+// sums per (range, query) are combined in FP64, together with a per-query error
+// estimate, by tc_combine_kernel; queries whose estimate is too large are recomputed by
+// the plain FP32 form.
 // Every mbarrier wait is bounded (%globaltimer); on expiry the kernel records an error
 // code, makes the other roles stop, waits for its own copies and MMAs, frees TMEM and
 // returns, and the host reports STAG_KDE_ETIMEDOUT.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <math.h>
+
+#include <stdlib.h>
 
 #include <algorithm>
 #include <mutex>
@@ -52,44 +60,52 @@ struct TcData {
     int64_t T = 0;       // number of point tiles
     int64_t n_pad = 0;   // T * BN
     __half *b_hi = nullptr, *b_lo = nullptr;  // [n_pad][Kp]
-    float *ccol = nullptr;                    // [T][BN + 4]: c * C(x) (+inf for padding points), then
-                                              // the tile's RMS radius and 3 zeros
+    __half *b_aug = nullptr;                  // [n_pad][16]: -g / (2 scale) in 3 FP16 pieces, then 0
+    __half *a_aug = nullptr;                  // [128][16]: s_a, s_a, s_a, 0, ...
+    float *tinfo = nullptr;                   // [T][4]: tile RMS radius, 0, 0, 0
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
     float *cg = nullptr;                      // [Kp]: global centre c_g
     double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
-    unsigned *vmax_bits = nullptr;            // max |v| (float bits)
-    float scale_v = 1.f;                      // power of two
-    CUtensorMap map_bhi, map_blo;
+    unsigned *vmax_bits = nullptr;            // max |x_k - c_t,k| (float bits)
+    unsigned *xmax_bits = nullptr;            // max |x_k - c_g,k| (float bits)
+    float *scales = nullptr;                  // [4]: scale_v, scale_u, kk, s_a
+    CUtensorMap map_bhi, map_blo, map_baug, map_aaug;
     // query-side scratch
     __half *a_hi = nullptr, *a_lo = nullptr;  // [m_cap][Kp]
     int64_t a_rows_cap = 0;
     CUtensorMap map_ahi, map_alo;
     float *rowterm = nullptr;  // [T][m_pad]
     int64_t rt_cap = 0;        // floats
-    unsigned *qmax_bits = nullptr;  // max |u| over the batch (float bits)
-    float *kk = nullptr;            // [1]: 2c / (scale_u scale_v)
-    float *unorm = nullptr;         // [m_cap]: ||q - c_g|| per query
+    float *unorm = nullptr;    // [m_cap]: ||q - c_g|| per query
+    int *qbad = nullptr;       // [m_cap]: query outside the FP16 range of the split
+    unsigned *ub = nullptr;    // [m_cap]: per-query exponent bound (order bits)
     int64_t unorm_cap = 0;
-    double *part_w = nullptr;       // [splits][m]: contribution-weighted tile radius sums
+    double *part_w = nullptr;  // [splits][m]: contribution-weighted tile radius sums
     int64_t part_w_cap = 0;
-    int *fix_idx = nullptr;         // [m_cap]: queries handed to the plain form
-    int *fix_count = nullptr;       // device counter
-    int64_t fix_cap = 0;
-    int *err = nullptr;             // device error code (timeouts)
-    int *err_host = nullptr;        // pinned mirror
+    int *fix_idx = nullptr;    // [m_cap]: queries handed to the plain form
+    int *fix_count = nullptr;  // device counter
+    int *err = nullptr;        // device error code (timeouts)
+    int *err_host = nullptr;   // pinned mirror
 };
 
 namespace {
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 constexpr int kErrTimeout = 1;
-constexpr float kShiftFloor = -0x1p100f;
-constexpr float kGuard = 0x1p64f;
 constexpr int BM = 128;  // queries per tile (MMA M, TMEM lanes)
 // Queries whose estimated tensor-core error exceeds this are recomputed with the plain
 // FP32 form; the estimate bounds the measured error from above (ratio <= ~0.96), so the
 // queries kept stay below ~7.2e-5 against the 1e-4 tolerance.
 constexpr double kTcErrThreshold = 7.5e-5;
+// Epilogue warps per TMEM lane quadrant (2 or 4); STAG_KDE_TC_EG overrides the default.
+int tc_epilogue_groups() {
+    static int eg = []() {
+        const char *e = getenv("STAG_KDE_TC_EG");
+        const int v = e ? atoi(e) : 4;
+        return v == 2 ? 2 : 4;
+    }();
+    return eg;
+}
 
 // ------------------------------------------------------------------ layout helpers
 template <int KP>
@@ -105,35 +121,42 @@ struct Geo {
     }
 };
 
-template <int KP, int BN, int SB, int SMETA, int AB>
+template <int KP, int BN, int SB, int SMETA, int AB, int EG>
 struct Cfg {
+    static constexpr int THREADS = 64 + 128 * EG;  // TMA warp, MMA warp, 4 * EG epilogue warps
     static constexpr int A_PLANE = BM * KP * 2;
     static constexpr int B_PLANE = BN * KP * 2;
-    static constexpr int A_BYTES = 2 * A_PLANE;
-    static constexpr int B_BYTES = 2 * B_PLANE;
-    static constexpr int META_BYTES = (BN + 4) * 4 + BM * 4;
+    static constexpr int A_AUG = BM * 16 * 2;
+    static constexpr int B_AUG = BN * 16 * 2;
+    static constexpr int A_BYTES = 2 * A_PLANE + A_AUG;
+    static constexpr int B_BYTES = 2 * B_PLANE + B_AUG;
+    static constexpr int META_BYTES = BM * 4 + 16;  // R of 128 queries, tile info
+    static constexpr int META_STRIDE = (META_BYTES + 127) / 128 * 128;
     static constexpr int OFF_A = 0;
     static constexpr int OFF_B = OFF_A + AB * A_BYTES;
     static constexpr int OFF_META = OFF_B + SB * B_BYTES;
-    static constexpr int OFF_MERGE = OFF_META + SMETA * META_BYTES;
-    static constexpr int OFF_BAR = OFF_MERGE + BM * 24;
+    static constexpr int OFF_MERGE = OFF_META + SMETA * META_STRIDE;
+    static constexpr int OFF_BAR = OFF_MERGE + BM * 24 * (EG - 1);
     static constexpr int NBAR = 2 * SB + 2 * SMETA + 2 * AB + 4 + 3;
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int BYTES = OFF_MISC + 64;
     static constexpr int SMEM = BYTES + 1024;  // + alignment slack
     static constexpr uint32_t TMEM_COLS = 2 * BN;
     static constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, BN);
+    static_assert(A_PLANE % 1024 == 0 && B_PLANE % 1024 == 0 && A_AUG % 1024 == 0 && B_AUG % 1024 == 0,
+                  "planes must keep 1024-byte alignment");
 };
 
 struct TcParams {
-    const float *ccol;     // [T][BN]
+    const float *tinfo;    // [T][4]
     const float *rowterm;  // [T][m_pad]
-    const float *kk;       // device scalar
+    const float *scales;   // device: scale_v, scale_u, kk, s_a
+    const unsigned *ub;    // [m_pad]: per-query upper bound on every exponent (order bits)
     double *part_sum;
     float *part_shift;
     double *part_w;
     int *err;
-    int64_t m, m_pad, T, q_tiles, tiles_per_split, units;
+    int64_t m, m_pad, n, T, q_tiles, tiles_per_split, units;
 };
 
 __device__ __forceinline__ int cexp(float e) { return (int)fminf(fmaxf(e, -4000.f), 4000.f); }
@@ -151,15 +174,18 @@ __device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
 __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
     uint64_t d;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
+}
+
+__device__ __forceinline__ uint32_t float_order_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_bits_to_float(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
 struct RowState {
@@ -170,60 +196,50 @@ struct RowState {
     double w64;
 };
 
-// Sum of 2^(kk*D[j] - E - s - col[j]) over 32 columns, rescaling the row if needed.
+// Sum of 2^(kk*D[j] + nb) over the first `valid` of 32 columns (valid = 32 except in the
+// point set's last, padded tile); nb = -(c R + s) with the row's fixed shift s, which
+// bounds every exponent from above, so no term exceeds ~1 and no rescaling is needed.
 // Two independent packed accumulators keep the dependency chains short.
-__device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32], const float *__restrict__ col,
-                                          float kk, float E, float vrad) {
-    const uint64_t kk2 = pack2(kk, kk);
-    float nb = -(E + st.shift);
-    const uint64_t nb2 = pack2(nb, nb);
-    uint64_t acc_a = 0, acc_b = 0;  // {0.f, 0.f}
+__device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32], float kk, float nb, float vrad,
+                                          int valid) {
+    float cs;
+    if (valid == 32) {
+        const uint64_t kk2 = pack2(kk, kk);
+        const uint64_t nb2 = pack2(nb, nb);
+        uint64_t acc_a = 0, acc_b = 0;  // {0.f, 0.f}
 #pragma unroll
-    for (int j = 0; j < 32; j += 4) {
-        const float4 c4 = *reinterpret_cast<const float4 *>(col + j);
-        const uint64_t x01 = fma2(kk2, pack2(__uint_as_float(D[j]), __uint_as_float(D[j + 1])),
-                                  sub2(nb2, pack2(c4.x, c4.y)));
-        const uint64_t x23 = fma2(kk2, pack2(__uint_as_float(D[j + 2]), __uint_as_float(D[j + 3])),
-                                  sub2(nb2, pack2(c4.z, c4.w)));
-        float a0, a1, a2, a3;
-        unpack2(x01, a0, a1);
-        unpack2(x23, a2, a3);
-        acc_a = add2(acc_a, pack2(ptx::ex2_approx(a0), ptx::ex2_approx(a1)));
-        acc_b = add2(acc_b, pack2(ptx::ex2_approx(a2), ptx::ex2_approx(a3)));
-    }
-    float s0, s1, s2, s3;
-    unpack2(acc_a, s0, s1);
-    unpack2(acc_b, s2, s3);
-    float cs = (s0 + s1) + (s2 + s3);
-    if (!(cs <= kGuard)) {
-        // rare: first tile of a row, or a tile whose terms exceed the current shift by 2^64
-        float mx = -INFINITY;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) mx = fmaxf(mx, fmaf(kk, __uint_as_float(D[j]), -(E + col[j])));
-        const float s_new = fmaxf(ceilf(mx), kShiftFloor);
-        if (s_new > st.shift) {
-            const int de = cexp(st.shift - s_new);
-            st.acc32 = ldexpf(st.acc32, de);
-            st.acc64 = ldexp(st.acc64, de);
-            st.w32 = ldexpf(st.w32, de);
-            st.w64 = ldexp(st.w64, de);
-            st.shift = s_new;
+        for (int j = 0; j < 32; j += 4) {
+            const uint64_t x01 = fma2(kk2, pack2(__uint_as_float(D[j]), __uint_as_float(D[j + 1])), nb2);
+            const uint64_t x23 = fma2(kk2, pack2(__uint_as_float(D[j + 2]), __uint_as_float(D[j + 3])), nb2);
+            float a0, a1, a2, a3;
+            unpack2(x01, a0, a1);
+            unpack2(x23, a2, a3);
+            acc_a = add2(acc_a, pack2(ptx::ex2_approx(a0), ptx::ex2_approx(a1)));
+            acc_b = add2(acc_b, pack2(ptx::ex2_approx(a2), ptx::ex2_approx(a3)));
         }
-        nb = -(E + st.shift);
+        float s0, s1, s2, s3;
+        unpack2(acc_a, s0, s1);
+        unpack2(acc_b, s2, s3);
+        cs = (s0 + s1) + (s2 + s3);
+    } else {
         cs = 0.f;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) cs += ptx::ex2_approx(fmaf(kk, __uint_as_float(D[j]), nb - col[j]));
+        for (int j = 0; j < 32; ++j) {
+            const float e = ptx::ex2_approx(fmaf(kk, __uint_as_float(D[j]), nb));
+            cs += j < valid ? e : 0.f;
+        }
     }
     st.acc32 += cs;
     st.w32 = fmaf(cs, vrad, st.w32);
 }
 
-template <int KP, int BN, int SB, int SMETA, int AB>
-__global__ void __launch_bounds__(320, 1)
+template <int KP, int BN, int SB, int SMETA, int AB, int EG>
+__global__ void __launch_bounds__(64 + 128 * EG, 1) __maxnreg__(EG >= 4 ? 112 : 200)
 kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
-              const __grid_constant__ CUtensorMap map_bhi, const __grid_constant__ CUtensorMap map_blo,
+              const __grid_constant__ CUtensorMap map_aaug, const __grid_constant__ CUtensorMap map_bhi,
+              const __grid_constant__ CUtensorMap map_blo, const __grid_constant__ CUtensorMap map_baug,
               const TcParams p) {
-    using C = Cfg<KP, BN, SB, SMETA, AB>;
+    using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
     using G = Geo<KP>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -252,7 +268,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
         }
         for (int i = 0; i < SMETA; ++i) {
             ptx::mbar_init(&full_m[i], 1);
-            ptx::mbar_init(&empty_m[i], 8);
+            ptx::mbar_init(&empty_m[i], 4 * EG);
         }
         for (int i = 0; i < AB; ++i) {
             ptx::mbar_init(&a_full[i], 1);
@@ -260,9 +276,9 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
         }
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&acc_full[i], 1);
-            ptx::mbar_init(&acc_empty[i], 8);
+            ptx::mbar_init(&acc_empty[i], 4 * EG);
         }
-        ptx::mbar_init(merge_full, 4);
+        ptx::mbar_init(merge_full, 4 * (EG - 1));
         ptx::mbar_init(merge_empty, 4);
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
@@ -272,8 +288,10 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
     if (warp == 0 && lane == 0) {
         ptx::prefetch_tensormap(&map_ahi);
         ptx::prefetch_tensormap(&map_alo);
+        ptx::prefetch_tensormap(&map_aaug);
         ptx::prefetch_tensormap(&map_bhi);
         ptx::prefetch_tensormap(&map_blo);
+        ptx::prefetch_tensormap(&map_baug);
     }
     if (warp == 1) {
         ptx::tmem_alloc(tmem_holder, C::TMEM_COLS);
@@ -313,6 +331,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     ptx::tma_load_2d(abuf + C::A_PLANE + ch * BM * G::CW * 2, &map_alo, ch * G::CW, (int)(qt * BM),
                                      &a_full[ab]);
                 }
+                ptx::tma_load_2d(abuf + 2 * C::A_PLANE, &map_aaug, 0, 0, &a_full[ab]);
                 ++issued_a;
                 for (int64_t t = t0; t < t1; ++t, ++tcount) {
                     const int sb = tcount % SB;
@@ -329,6 +348,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                         ptx::tma_load_2d(bbuf + C::B_PLANE + ch * BN * G::CW * 2, &map_blo, ch * G::CW, (int)(t * BN),
                                          &full_b[sb]);
                     }
+                    ptx::tma_load_2d(bbuf + 2 * C::B_PLANE, &map_baug, 0, (int)(t * BN), &full_b[sb]);
                     ++issued_b;
                     const int ms = tcount % SMETA;
                     if (!ptx::mbar_wait_bounded(&empty_m[ms], ((tcount / SMETA) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
@@ -336,10 +356,10 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                         ok = false;
                         break;
                     }
-                    uint8_t *mbuf = smem + C::OFF_META + ms * C::META_BYTES;
+                    uint8_t *mbuf = smem + C::OFF_META + ms * C::META_STRIDE;
                     ptx::mbar_arrive_expect_tx(&full_m[ms], C::META_BYTES);
-                    ptx::bulk_load(mbuf, p.ccol + t * (BN + 4), (BN + 4) * 4, &full_m[ms]);
-                    ptx::bulk_load(mbuf + (BN + 4) * 4, p.rowterm + t * p.m_pad + qt * BM, BM * 4, &full_m[ms]);
+                    ptx::bulk_load(mbuf, p.rowterm + t * p.m_pad + qt * BM, BM * 4, &full_m[ms]);
+                    ptx::bulk_load(mbuf + BM * 4, p.tinfo + t * 4, 16, &full_m[ms]);
                     ++issued_m;
                 }
             }
@@ -407,6 +427,12 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                             accumulate = 1;
                         }
                     }
+                    {
+                        // the point term: constant A column x (-g/2) pieces, one K = 16 step
+                        const uint64_t ad = ptx::smem_desc(abase + 2 * C::A_PLANE, 16, 256, ptx::kSw32);
+                        const uint64_t bd = ptx::smem_desc(bbase + 2 * C::B_PLANE, 16, 256, ptx::kSw32);
+                        ptx::mma_f16(d_tmem, ad, bd, C::IDESC, 1);
+                    }
                     ptx::mma_commit(&empty_b[sb]);
                     ptx::mma_commit(&acc_full[acc]);
                 }
@@ -418,20 +444,27 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
             ptx::mbar_wait_bounded(drain, 0, 100000000ull, &no_abort);
         }
     } else {
-        // ------------------------------------------------------------ epilogue (8 warps)
-        const int ew = warp - 2;             // 0..7
+        // ------------------------------------------------------------ epilogue (4 * EG warps)
+        const int ew = warp - 2;             // 0 .. 4*EG-1
         const int quad = warp & 3;           // TMEM lane quadrant this warp may access
-        const int half = ew >> 2;            // column half
+        const int grp = ew >> 2;             // column group: columns [grp*BN/EG, (grp+1)*BN/EG)
         const int row = quad * 32 + lane;    // query row within the tile
-        const float kk = *p.kk;
-        float *merge = reinterpret_cast<float *>(smem + C::OFF_MERGE);
+        constexpr int COLS = BN / EG;
+        constexpr int NCH = COLS / 32;
+        static_assert(COLS % 32 == 0, "column group must be whole 32-column chunks");
+        const float kk = p.scales[2];
+        double *msum = reinterpret_cast<double *>(smem + C::OFF_MERGE);   // [EG-1][BM]
+        double *mw = msum + (EG - 1) * BM;                                 // [EG-1][BM]
+        float *mshift = reinterpret_cast<float *>(mw + (EG - 1) * BM);     // [EG-1][BM]
         uint32_t tcount = 0, ucount = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
             const int64_t split = u / p.q_tiles, qt = u % p.q_tiles;
             const int64_t t0 = split * p.tiles_per_split;
             const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
-            RowState st{kShiftFloor, 0.f, 0.0, 0.f, 0.0};
+            // the row's fixed shift: ceil of an upper bound on every exponent of the row
+            const float s_row = ceilf(order_bits_to_float(p.ub[qt * BM + row]));
+            RowState st{s_row, 0.f, 0.0, 0.f, 0.0};
             for (int64_t t = t0; t < t1; ++t, ++tcount) {
                 const int acc = tcount & 1;
                 const int ms = tcount % SMETA;
@@ -445,41 +478,59 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     break;
                 }
                 ptx::tc_fence_after();
-                const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_BYTES);
-                const float E = meta[BN + 4 + row];
-                const float vrad = meta[BN];
-                const float *col = meta + half * (BN / 2);
-                const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + half * (BN / 2);
-                constexpr int NCH = BN / 2 / 32;
-                // software pipeline: the TMEM load of chunk c+1 is in flight while chunk c
-                // is processed (tcgen05.wait::ld waits for every load issued before it)
-                uint32_t Da[32], Db[32];
-                ptx::tmem_ld_32x32b_x32(taddr, Da);
-                ptx::tmem_ld_wait();
-                ptx::reg_fence32(Da);
+                const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
+                const float nb = -(meta[row] + st.shift);
+                const float vrad = meta[BM];
+                // real points among this warp's columns (only the last tile is padded)
+                const int64_t col0 = t * BN + grp * COLS;
+                const int vcols = (int)max((int64_t)0, min((int64_t)COLS, p.n - col0));
+                const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS;
+                if constexpr (EG >= 4 || NCH == 1) {
+                    // enough warps per scheduler to hide the TMEM load latency: one buffer
 #pragma unroll
-                for (int c = 0; c < NCH; ++c) {
-                    if (c + 1 < NCH) {
-                        if (c & 1)
-                            ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Da);
-                        else
-                            ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Db);
-                    } else {
-                        // every TMEM column of this buffer has been read: hand it back
-                        ptx::tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
-                    }
-                    if (c & 1)
-                        epi_chunk(st, Db, col + c * 32, kk, E, vrad);
-                    else
-                        epi_chunk(st, Da, col + c * 32, kk, E, vrad);
-                    if (c + 1 < NCH) {
+                    for (int c = 0; c < NCH; ++c) {
+                        uint32_t Da[32];
+                        ptx::tmem_ld_32x32b_x32(taddr + c * 32, Da);
                         ptx::tmem_ld_wait();
+                        ptx::reg_fence32(Da);
+                        if (c + 1 == NCH) {
+                            ptx::tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+                        }
+                        epi_chunk(st, Da, kk, nb, vrad, min(32, max(0, vcols - c * 32)));
+                    }
+                } else {
+                    // software pipeline: the TMEM load of chunk c+1 is in flight while chunk
+                    // c is processed (tcgen05.wait::ld waits for every load issued before it)
+                    uint32_t Da[32], Db[32];
+                    ptx::tmem_ld_32x32b_x32(taddr, Da);
+                    ptx::tmem_ld_wait();
+                    ptx::reg_fence32(Da);
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) {
+                        if (c + 1 < NCH) {
+                            if (c & 1)
+                                ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Da);
+                            else
+                                ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Db);
+                        } else {
+                            // every TMEM column of this buffer has been read: hand it back
+                            ptx::tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+                        }
                         if (c & 1)
-                            ptx::reg_fence32(Da);
+                            epi_chunk(st, Db, kk, nb, vrad, min(32, max(0, vcols - c * 32)));
                         else
-                            ptx::reg_fence32(Db);
+                            epi_chunk(st, Da, kk, nb, vrad, min(32, max(0, vcols - c * 32)));
+                        if (c + 1 < NCH) {
+                            ptx::tmem_ld_wait();
+                            if (c & 1)
+                                ptx::reg_fence32(Da);
+                            else
+                                ptx::reg_fence32(Db);
+                        }
                     }
                 }
                 __syncwarp();
@@ -490,20 +541,18 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                 st.w32 = 0.f;
             }
             if (!ok) break;
-            // merge the two column halves of each row (half 1 hands its sums to half 0
-            // through shared memory), then store the unit's partials
-            double *msum = reinterpret_cast<double *>(merge);
-            double *mw = msum + BM;
-            float *mshift = merge + 4 * BM;
-            if (half == 1) {
+            // merge the column groups of each row (groups 1.. hand their sums to group 0
+            // through shared memory; group 0 adds them in group order), then store the
+            // unit's partials
+            if (grp > 0) {
                 const bool got = ptx::mbar_wait_bounded(merge_empty, (ucount & 1) ^ 1, kWaitLimitNs, abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
                     timed_out();
                     break;
                 }
-                msum[row] = st.acc64;
-                mw[row] = st.w64;
-                mshift[row] = st.shift;
+                msum[(grp - 1) * BM + row] = st.acc64;
+                mw[(grp - 1) * BM + row] = st.w64;
+                mshift[(grp - 1) * BM + row] = st.shift;
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(merge_full);
             } else {
@@ -512,15 +561,26 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     timed_out();
                     break;
                 }
-                const double oa = msum[row];
-                const double ow = mw[row];
-                const float os = mshift[row];
+                float os[EG - 1];
+                double oa[EG - 1], ow[EG - 1];
+                float sm = st.shift;
+#pragma unroll
+                for (int g = 0; g < EG - 1; ++g) {
+                    oa[g] = msum[g * BM + row];
+                    ow[g] = mw[g * BM + row];
+                    os[g] = mshift[g * BM + row];
+                    sm = fmaxf(sm, os[g]);
+                }
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(merge_empty);
-                const float sm = fmaxf(st.shift, os);
-                const int e0 = cexp(st.shift - sm), e1 = cexp(os - sm);
-                const double tot = ldexp(st.acc64, e0) + ldexp(oa, e1);
-                const double wt = ldexp(st.w64, e0) + ldexp(ow, e1);
+                const int e0 = cexp(st.shift - sm);
+                double tot = ldexp(st.acc64, e0), wt = ldexp(st.w64, e0);
+#pragma unroll
+                for (int g = 0; g < EG - 1; ++g) {
+                    const int e = cexp(os[g] - sm);
+                    tot += ldexp(oa[g], e);
+                    wt += ldexp(ow[g], e);
+                }
                 const int64_t q = qt * BM + row;
                 if (q < p.m) {
                     p.part_sum[split * p.m + q] = tot;
@@ -570,35 +630,66 @@ __device__ __forceinline__ void atomic_max_pos(unsigned *bits, float v) {
     atomicMax(bits, __float_as_uint(fabsf(v)));
 }
 
-// max over points of |x - c_t| (each coordinate)
-__global__ void tc_vmax_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
-                               const float *__restrict__ cent, unsigned *vmax) {
+// max over points and coordinates of |x_k - c_k|, with c = the point's tile centre
+// (per_tile = true) or the global centre
+__global__ void tc_maxabs_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
+                                 const float *__restrict__ cent, const float *__restrict__ cg, bool per_tile,
+                                 unsigned *out) {
     float mx = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * d; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / d, k = i % d;
-        mx = fmaxf(mx, fabsf(X[i] - cent[(r / BN) * Kp + k]));
+        const float c = per_tile ? cent[(r / BN) * Kp + k] : cg[k];
+        mx = fmaxf(mx, fabsf(X[i] - c));
     }
     for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_pos(vmax, mx);
+    if ((threadIdx.x & 31) == 0) atomic_max_pos(out, mx);
 }
 
-__device__ __forceinline__ float pow2_scale(unsigned maxbits) {
-    // largest power of two s with max * s <= 2^14 (FP16 headroom for hi + lo sums)
-    const float mx = __uint_as_float(maxbits);
-    if (!(mx > 0.f) || !isfinite(mx)) return 1.f;
+__device__ __forceinline__ double pow2_at_or_above(double x) {
     int e;
-    frexpf(mx, &e);  // mx in [2^(e-1), 2^e)
-    return ldexpf(1.f, 14 - e);
+    frexp(x, &e);  // x in [2^(e-1), 2^e)
+    return ldexp(1.0, e);
 }
 
-// FP16 hi/lo split of v = (x - c_t) * scale_v and the column term c * (|v~|^2 + 2 D_t . v~)
-// computed in FP64 from the represented v~ = (hi + lo) / scale_v.
+// Power-of-two scales of the split (one thread):
+//   scale_v: max |v_k| * scale_v < 2^10          (v = x - c_t)
+//   scale_u: max |x_k - c_g| * scale_u < 2^9    (queries up to 64x farther still fit FP16)
+//   kk = 2c / (scale_u scale_v)
+//   s_a: the point-term pieces g * scale_u * scale_v / (2 s_a) stay below 2^14, using
+//        |g| <= d vmax^2 + 2 d xmax vmax; for d <= 128 this keeps s_a <= 2^13
+// and the constant A column [s_a, s_a, s_a, 0, ...] of every query row. FP16 keeps 11
+// significant bits at any magnitude, so the modest ranges cost no precision and leave
+// room for the u . v sums and the point term in the same FP32 accumulator.
+__global__ void tc_scales_kernel(const unsigned *__restrict__ vmax, const unsigned *__restrict__ xmax, int64_t d,
+                                 double c, float *__restrict__ scales, __half *__restrict__ a_aug) {
+    __shared__ float sa_sh;
+    if (threadIdx.x == 0) {
+        const double vm = (double)__uint_as_float(*vmax), xm = (double)__uint_as_float(*xmax);
+        const double sv = vm > 0.0 && isfinite(vm) ? 0x1p10 / pow2_at_or_above(vm) : 1.0;
+        const double su = xm > 0.0 && isfinite(xm) ? 0x1p9 / pow2_at_or_above(xm) : 1.0;
+        const double gmax = (double)d * vm * vm + 2.0 * (double)d * xm * vm;
+        double sa = gmax > 0.0 ? pow2_at_or_above(gmax * su * sv * 0.5) * 0x1p-14 : 1.0;
+        sa = fmin(fmax(sa, 0x1p-14), 0x1p15);
+        scales[0] = (float)sv;
+        scales[1] = (float)su;
+        scales[2] = (float)(2.0 * c / (su * sv));
+        scales[3] = (float)sa;
+        sa_sh = (float)sa;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < BM * 16; i += blockDim.x) a_aug[i] = __float2half_rn((i % 16) < 3 ? sa_sh : 0.f);
+}
+
+// Splits x - c_t into FP16 hi/lo (scaled by scale_v) and the point term
+// g = |v~|^2 + 2 D_t . v~ (FP64, from the represented v~ = (hi + lo) / scale_v) into three
+// FP16 pieces of -g * scale_u * scale_v / (2 s_a). Padding points are all zero (the
+// epilogue masks them).
 __global__ void tc_split_points_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp, int64_t n_pad,
                                        const float *__restrict__ cent, const float *__restrict__ cg,
-                                       const unsigned *__restrict__ vmax, double c, __half *__restrict__ bhi,
-                                       __half *__restrict__ blo, float *__restrict__ ccol) {
-    const float sv = pow2_scale(*vmax);
-    const double inv = 1.0 / (double)sv;
+                                       const float *__restrict__ scales, __half *__restrict__ bhi,
+                                       __half *__restrict__ blo, __half *__restrict__ baug) {
+    const double sv = scales[0], su = scales[1], sa = scales[3];
+    const double inv = 1.0 / sv;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_pad; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = i / BN;
         double nv2 = 0.0, dv = 0.0;
@@ -606,7 +697,7 @@ __global__ void tc_split_points_kernel(const float *__restrict__ X, int64_t n, i
             __half h = __float2half_rn(0.f), l = __float2half_rn(0.f);
             if (i < n && k < d) {
                 const float ct = cent[t * Kp + k];
-                const double v = ((double)X[i * d + k] - (double)ct) * (double)sv;
+                const double v = ((double)X[i * d + k] - (double)ct) * sv;
                 h = __double2half(v);
                 l = __double2half(v - (double)__half2float(h));
                 const double vr = ((double)__half2float(h) + (double)__half2float(l)) * inv;
@@ -616,18 +707,27 @@ __global__ void tc_split_points_kernel(const float *__restrict__ X, int64_t n, i
             bhi[i * Kp + k] = h;
             blo[i * Kp + k] = l;
         }
-        ccol[t * (BN + 4) + (i - t * BN)] = i < n ? (float)(c * (nv2 + 2.0 * dv)) : INFINITY;
+        double y = i < n ? -(nv2 + 2.0 * dv) * su * sv / (2.0 * sa) : 0.0;
+        for (int k = 0; k < 16; ++k) {
+            __half pc = __float2half_rn(0.f);
+            if (k < 3) {
+                pc = __double2half(y);
+                y -= (double)__half2float(pc);
+            }
+            baug[i * 16 + k] = pc;
+        }
     }
 }
 
 // Per tile: the RMS distance of its points from the tile centre (used by the per-query
-// error estimate), stored after the tile's column terms.
+// error estimate).
 __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
-                                      const float *__restrict__ cent, float *__restrict__ ccol) {
+                                      const float *__restrict__ cent, float *__restrict__ tinfo) {
     __shared__ double red[128];
+    __shared__ double redm[128];
     const int64_t t = blockIdx.x;
     const int64_t r0 = t * BN, cnt = min((int64_t)BN, n - r0);
-    double acc = 0.0;
+    double acc = 0.0, mx = 0.0;
     for (int64_t r = threadIdx.x; r < cnt; r += blockDim.x) {
         double s2 = 0.0;
         for (int64_t k = 0; k < d; ++k) {
@@ -635,46 +735,47 @@ __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, in
             s2 += v * v;
         }
         acc += s2;
+        mx = fmax(mx, s2);
     }
     red[threadIdx.x] = acc;
+    redm[threadIdx.x] = mx;
     __syncthreads();
     for (int o = 64; o; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        if (threadIdx.x < o) {
+            red[threadIdx.x] += red[threadIdx.x + o];
+            redm[threadIdx.x] = fmax(redm[threadIdx.x], redm[threadIdx.x + o]);
+        }
         __syncthreads();
     }
-    if (threadIdx.x < 4) {
-        float v = 0.f;
-        if (threadIdx.x == 0 && cnt > 0) v = (float)sqrt(red[0] / (double)cnt);
-        ccol[t * (BN + 4) + BN + threadIdx.x] = v;
+    if (threadIdx.x == 0) {
+        tinfo[t * 4 + 0] = cnt > 0 ? (float)sqrt(red[0] / (double)cnt) : 0.f;  // RMS radius
+        // max radius, rounded up so that it bounds the FP32 distances too
+        tinfo[t * 4 + 1] = cnt > 0 ? (float)(sqrt(redm[0]) * (1.0 + 1e-6)) : 0.f;
+        tinfo[t * 4 + 2] = 0.f;
+        tinfo[t * 4 + 3] = 0.f;
     }
 }
 
-__global__ void tc_qmax_kernel(const float *__restrict__ Q, int64_t m, int64_t d, const float *__restrict__ cg,
-                               unsigned *qmax) {
-    float mx = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m * d; i += (int64_t)gridDim.x * blockDim.x)
-        mx = fmaxf(mx, fabsf(Q[i] - cg[i % d]));
-    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_pos(qmax, mx);
-}
-
-// FP16 hi/lo split of u = (q - c_g) * scale_u for m_pad rows (padding rows zero), and
-// kk = 2c / (scale_u scale_v).
+// FP16 hi/lo split of u = (q - c_g) * scale_u for m_pad rows (padding rows zero). A query
+// farther from the data than the split's range is zeroed and marked in qbad; the combine
+// hands it to the plain FP32 form.
 __global__ void tc_split_queries_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
-                                        const float *__restrict__ cg, const unsigned *__restrict__ qmax,
-                                        const unsigned *__restrict__ vmax, double c, __half *__restrict__ ahi,
-                                        __half *__restrict__ alo, float *__restrict__ kk) {
-    const float su = pow2_scale(*qmax);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *kk = (float)(2.0 * c / ((double)su * (double)pow2_scale(*vmax)));
+                                        const float *__restrict__ cg, const float *__restrict__ scales,
+                                        __half *__restrict__ ahi, __half *__restrict__ alo, int *__restrict__ qbad) {
+    const double su = scales[1];
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_pad * Kp;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / Kp;
         const int k = (int)(i % Kp);
         __half h = __float2half_rn(0.f), l = __float2half_rn(0.f);
         if (r < m && k < d) {
-            const double u = ((double)Q[r * d + k] - (double)cg[k]) * (double)su;
-            h = __double2half(u);
-            l = __double2half(u - (double)__half2float(h));
+            const double u = ((double)Q[r * d + k] - (double)cg[k]) * su;
+            if (fabs(u) < 0x1p15) {
+                h = __double2half(u);
+                l = __double2half(u - (double)__half2float(h));
+            } else {
+                qbad[r] = 1;
+            }
         }
         ahi[i] = h;
         alo[i] = l;
@@ -686,7 +787,8 @@ __global__ void tc_split_queries_kernel(const float *__restrict__ Q, int64_t m, 
 __global__ void __launch_bounds__(128)
 tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
                   const float *__restrict__ cent, int64_t T, int tiles_per_block, float c, float *__restrict__ R,
-                  const float *__restrict__ cg, float *__restrict__ unorm) {
+                  const float *__restrict__ cg, float *__restrict__ unorm, const float *__restrict__ tinfo,
+                  unsigned *__restrict__ ub) {
     extern __shared__ float sq[];  // [Kp][128]
     const int64_t q0 = (int64_t)blockIdx.x * 128;
     const int r = threadIdx.x;
@@ -706,6 +808,11 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
     const bool real = q0 + r < m;
+    // upper bound on the exponent -c ||q - x||^2 over the tiles of this block: every x of
+    // tile t lies within the tile's max radius rho_t of c_t, so
+    //     -c ||q - x||^2 <= -( max(0, sqrt(c R') - sqrt(c) rho_t) )^2,  R' = ||q - c_t||^2
+    const float sqc = sqrtf(c);
+    float ubest = -INFINITY;
     for (int64_t t = ta; t < tb; ++t) {
         const float4 *ct = reinterpret_cast<const float4 *>(cent + t * Kp);
         float s0 = 0.f, s1 = 0.f;
@@ -720,8 +827,13 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int
             s0 = fmaf(d2, d2, s0);
             s1 = fmaf(d3, d3, s1);
         }
-        R[t * m_pad + q0 + r] = real ? c * (s0 + s1) : 0.f;
+        const float cr = c * (s0 + s1);
+        R[t * m_pad + q0 + r] = real ? cr : 0.f;
+        // slack of a few ulps so that the bound holds for the FP32-computed exponents too
+        const float gap = fmaxf(0.f, sqrtf(cr) * (1.f - 1e-5f) - sqc * __ldg(tinfo + t * 4 + 1));
+        ubest = fmaxf(ubest, -gap * gap);
     }
+    if (tb > ta) atomicMax(ub + q0 + r, float_order_bits(real ? ubest : 0.f));
 }
 
 // FP64 combine of the per-split partials (as kde_combine.cu) plus the per-query error
@@ -731,8 +843,9 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int
 // est > thr (or an empty sum) are appended to fix_idx for the plain FP32 form.
 __global__ void tc_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
                                   const double *__restrict__ part_w, int64_t m, int splits, double scale,
-                                  const float *__restrict__ unorm, double a, double thr, double *__restrict__ out,
-                                  int *__restrict__ fix_idx, int *__restrict__ fix_count) {
+                                  const float *__restrict__ unorm, const int *__restrict__ qbad, double a,
+                                  double thr, double *__restrict__ out, int *__restrict__ fix_idx,
+                                  int *__restrict__ fix_count) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         float smax = -INFINITY;
         for (int k = 0; k < splits; ++k) smax = fmaxf(smax, part_shift[(int64_t)k * m + j]);
@@ -743,7 +856,9 @@ __global__ void tc_combine_kernel(const double *__restrict__ part_sum, const flo
             wt += ldexp(part_w[(int64_t)k * m + j], e);
         }
         out[j] = ldexp(tot, cexp(smax)) * scale;
-        const double est = tot > 0.0 ? 0x1p-21 * a * (double)unorm[j] * (wt / tot) : INFINITY;
+        // tot is in units of 2^smax, a bound on every term: below 2^-40 the bound was too
+        // loose for the fixed shift (terms under 2^-126 of it were flushed)
+        const double est = (tot >= 0x1p-40 && !qbad[j]) ? 0x1p-21 * a * (double)unorm[j] * (wt / tot) : INFINITY;
         if (est > thr && fix_idx) fix_idx[atomicAdd(fix_count, 1)] = (int)j;
     }
 }
@@ -767,13 +882,13 @@ PFN_encodeTiled get_encode() {
     return fn;
 }
 
-// 2-D FP16 tensor map over a [rows][Kp] plane with box {min(Kp,64), box_rows}.
-int make_map(CUtensorMap *map, void *base, int64_t rows, int Kp, int box_rows) {
+// 2-D FP16 tensor map over a [rows][width] plane with box {min(width,64), box_rows}.
+int make_map(CUtensorMap *map, void *base, int64_t rows, int width, int box_rows) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) return fail(STAG_KDE_ECUDA, "cuTensorMapEncodeTiled unavailable");
-    const int cw = Kp < 64 ? Kp : 64;
-    cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+    const int cw = width < 64 ? width : 64;
+    cuuint64_t dims[2] = {(cuuint64_t)width, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)width * 2};
     cuuint32_t box[2] = {(cuuint32_t)cw, (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     const CUtensorMapSwizzle sw = cw == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
@@ -797,10 +912,10 @@ int bn_for(int Kp) { return Kp >= 128 ? 128 : 256; }
 
 int grid_for(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_div(total, threads), 152 * 16); }
 
-template <int KP, int BN, int SB, int SMETA, int AB>
+template <int KP, int BN, int SB, int SMETA, int AB, int EG>
 int launch_tc(stag_kde *h, const TcParams &prm, cudaStream_t s) {
-    using C = Cfg<KP, BN, SB, SMETA, AB>;
-    auto kern = kde_tc_kernel<KP, BN, SB, SMETA, AB>;
+    using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
+    auto kern = kde_tc_kernel<KP, BN, SB, SMETA, AB, EG>;
     static_assert(C::SMEM <= 232448, "shared memory budget");
     // at least 116 KB so that no two CTAs share an SM (each holds up to 512 TMEM columns)
     const int smem = std::max(C::SMEM, 118 * 1024);
@@ -809,7 +924,8 @@ int launch_tc(stag_kde *h, const TcParams &prm, cudaStream_t s) {
     TcData *tc = h->tc;
     count_launch();
     prof_start(h, s);
-    kern<<<grid, 320, smem, s>>>(tc->map_ahi, tc->map_alo, tc->map_bhi, tc->map_blo, prm);
+    kern<<<grid, C::THREADS, smem, s>>>(tc->map_ahi, tc->map_alo, tc->map_aaug, tc->map_bhi, tc->map_blo,
+                                        tc->map_baug, prm);
     prof_stop(h, s, (double)prm.m * (double)h->n);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
@@ -826,21 +942,25 @@ void tc_free(stag_kde *h) {
     if (!tc) return;
     cudaFree(tc->b_hi);
     cudaFree(tc->b_lo);
-    cudaFree(tc->ccol);
+    cudaFree(tc->b_aug);
+    cudaFree(tc->a_aug);
+    cudaFree(tc->tinfo);
     cudaFree(tc->cent);
     cudaFree(tc->cg);
     cudaFree(tc->tsum);
     cudaFree(tc->vmax_bits);
+    cudaFree(tc->xmax_bits);
+    cudaFree(tc->scales);
     cudaFree(tc->a_hi);
     cudaFree(tc->a_lo);
     cudaFree(tc->rowterm);
-    cudaFree(tc->qmax_bits);
-    cudaFree(tc->kk);
-    cudaFree(tc->err);
     cudaFree(tc->unorm);
+    cudaFree(tc->qbad);
+    cudaFree(tc->ub);
     cudaFree(tc->part_w);
     cudaFree(tc->fix_idx);
     cudaFree(tc->fix_count);
+    cudaFree(tc->err);
     if (tc->err_host) cudaFreeHost(tc->err_host);
     delete tc;
     h->tc = nullptr;
@@ -858,31 +978,38 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     const int Kp = tc->Kp;
     STAG_CUDA_TRY(cudaMalloc(&tc->b_hi, tc->n_pad * Kp * sizeof(__half)));
     STAG_CUDA_TRY(cudaMalloc(&tc->b_lo, tc->n_pad * Kp * sizeof(__half)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->ccol, tc->T * (tc->BN + 4) * sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->b_aug, tc->n_pad * 16 * sizeof(__half)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->a_aug, BM * 16 * sizeof(__half)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->tinfo, tc->T * 4 * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->cent, tc->T * Kp * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->cg, Kp * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->tsum, tc->T * Kp * sizeof(double)));
     STAG_CUDA_TRY(cudaMalloc(&tc->vmax_bits, sizeof(unsigned)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->qmax_bits, sizeof(unsigned)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->kk, sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->xmax_bits, sizeof(unsigned)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->scales, 4 * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->err, sizeof(int)));
     STAG_CUDA_TRY(cudaMallocHost(&tc->err_host, sizeof(int)));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->err, 0, sizeof(int), s));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->vmax_bits, 0, sizeof(unsigned), s));
+    STAG_CUDA_TRY(cudaMemsetAsync(tc->xmax_bits, 0, sizeof(unsigned), s));
 
-    count_launch(5);
+    const double c = h->a * 1.4426950408889634;
+    count_launch(7);
     tc_centres_kernel<<<(unsigned)tc->T, 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->tsum, tc->cent);
     tc_global_centre_kernel<<<1, 128, 0, s>>>(tc->tsum, tc->T, Kp, h->n, h->d, tc->cg);
-    tc_vmax_kernel<<<grid_for(h->n * h->d, 256), 256, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->vmax_bits);
-    const double c = h->a * 1.4426950408889634;
+    tc_maxabs_kernel<<<grid_for(h->n * h->d, 256), 256, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->cg, true,
+                                                               tc->vmax_bits);
+    tc_maxabs_kernel<<<grid_for(h->n * h->d, 256), 256, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->cg, false,
+                                                               tc->xmax_bits);
+    tc_scales_kernel<<<1, 256, 0, s>>>(tc->vmax_bits, tc->xmax_bits, h->d, c, tc->scales, tc->a_aug);
     tc_split_points_kernel<<<grid_for(tc->n_pad, 128), 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->n_pad, tc->cent,
-                                                                    tc->cg, tc->vmax_bits, c, tc->b_hi, tc->b_lo,
-                                                                    tc->ccol);
-    count_launch();
-    tc_tile_radius_kernel<<<(unsigned)tc->T, 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->ccol);
+                                                                    tc->cg, tc->scales, tc->b_hi, tc->b_lo, tc->b_aug);
+    tc_tile_radius_kernel<<<(unsigned)tc->T, 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->tinfo);
     STAG_CUDA_TRY(cudaGetLastError());
     int rc = make_map(&tc->map_bhi, tc->b_hi, tc->n_pad, Kp, tc->BN);
     if (!rc) rc = make_map(&tc->map_blo, tc->b_lo, tc->n_pad, Kp, tc->BN);
+    if (!rc) rc = make_map(&tc->map_baug, tc->b_aug, tc->n_pad, 16, tc->BN);
+    if (!rc) rc = make_map(&tc->map_aaug, tc->a_aug, BM, 16, BM);
     return rc;
 }
 
@@ -903,11 +1030,17 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
     }
     if (tc->unorm_cap < m_pad) {
         cudaFree(tc->unorm);
+        cudaFree(tc->qbad);
+        cudaFree(tc->ub);
         cudaFree(tc->fix_idx);
         tc->unorm = nullptr;
+        tc->qbad = nullptr;
+        tc->ub = nullptr;
         tc->fix_idx = nullptr;
         tc->unorm_cap = 0;
         STAG_CUDA_TRY(cudaMalloc(&tc->unorm, m_pad * sizeof(float)));
+        STAG_CUDA_TRY(cudaMalloc(&tc->qbad, m_pad * sizeof(int)));
+        STAG_CUDA_TRY(cudaMalloc(&tc->ub, m_pad * sizeof(unsigned)));
         STAG_CUDA_TRY(cudaMalloc(&tc->fix_idx, m_pad * sizeof(int)));
         tc->unorm_cap = m_pad;
     }
@@ -934,11 +1067,11 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
         if (rc) return rc;
     }
     const double c = h->a * 1.4426950408889634;
-    STAG_CUDA_TRY(cudaMemsetAsync(tc->qmax_bits, 0, sizeof(unsigned), s));
-    count_launch(3);
-    tc_qmax_kernel<<<grid_for(m * h->d, 256), 256, 0, s>>>(dQ, m, h->d, tc->cg, tc->qmax_bits);
-    tc_split_queries_kernel<<<grid_for(m_pad * Kp, 256), 256, 0, s>>>(dQ, m, h->d, Kp, m_pad, tc->cg, tc->qmax_bits,
-                                                                      tc->vmax_bits, c, tc->a_hi, tc->a_lo, tc->kk);
+    STAG_CUDA_TRY(cudaMemsetAsync(tc->qbad, 0, m_pad * sizeof(int), s));
+    STAG_CUDA_TRY(cudaMemsetAsync(tc->ub, 0, m_pad * sizeof(unsigned), s));
+    count_launch(2);
+    tc_split_queries_kernel<<<grid_for(m_pad * Kp, 256), 256, 0, s>>>(dQ, m, h->d, Kp, m_pad, tc->cg, tc->scales,
+                                                                      tc->a_hi, tc->a_lo, tc->qbad);
     {
         const int tpb = 64;
         static std::once_flag attr_once;
@@ -947,7 +1080,8 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
         });
         dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
         tc_rowterm_kernel<<<grid, 128, Kp * 128 * sizeof(float), s>>>(dQ, m, h->d, Kp, m_pad, tc->cent, tc->T, tpb,
-                                                                      (float)c, tc->rowterm, tc->cg, tc->unorm);
+                                                                      (float)c, tc->rowterm, tc->cg, tc->unorm,
+                                                                      tc->tinfo, tc->ub);
     }
     STAG_CUDA_TRY(cudaGetLastError());
 
@@ -967,24 +1101,31 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
         tc->part_w_cap = splits * m;
     }
     TcParams prm;
-    prm.ccol = tc->ccol;
+    prm.tinfo = tc->tinfo;
     prm.rowterm = tc->rowterm;
-    prm.kk = tc->kk;
+    prm.scales = tc->scales;
+    prm.ub = tc->ub;
     prm.part_sum = h->part.sum;
     prm.part_shift = h->part.shift;
     prm.part_w = tc->part_w;
     prm.err = tc->err;
     prm.m = m;
     prm.m_pad = m_pad;
+    prm.n = h->n;
     prm.T = tc->T;
     prm.q_tiles = q_tiles;
     prm.tiles_per_split = tps;
     prm.units = q_tiles * splits;
-    switch (Kp) {
-        case 16: rc = launch_tc<16, 256, 4, 8, 2>(h, prm, s); break;
-        case 32: rc = launch_tc<32, 256, 4, 8, 2>(h, prm, s); break;
-        case 64: rc = launch_tc<64, 256, 2, 8, 2>(h, prm, s); break;
-        case 128: rc = launch_tc<128, 128, 2, 8, 1>(h, prm, s); break;
+    const int eg = tc_epilogue_groups();
+    switch (Kp * 10 + eg) {
+        case 162: rc = launch_tc<16, 256, 4, 8, 2, 2>(h, prm, s); break;
+        case 164: rc = launch_tc<16, 256, 4, 8, 2, 4>(h, prm, s); break;
+        case 322: rc = launch_tc<32, 256, 4, 8, 2, 2>(h, prm, s); break;
+        case 324: rc = launch_tc<32, 256, 4, 8, 2, 4>(h, prm, s); break;
+        case 642: rc = launch_tc<64, 256, 2, 8, 1, 2>(h, prm, s); break;
+        case 644: rc = launch_tc<64, 256, 2, 8, 1, 4>(h, prm, s); break;
+        case 1282: rc = launch_tc<128, 128, 2, 8, 1, 2>(h, prm, s); break;
+        case 1284: rc = launch_tc<128, 128, 2, 8, 1, 4>(h, prm, s); break;
         default: return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported d");
     }
     if (rc) return rc;
@@ -993,7 +1134,7 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
     count_launch();
     tc_combine_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
         h->part.sum, h->part.shift, tc->part_w, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0, tc->unorm,
-        h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
+        tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
     STAG_CUDA_TRY(cudaGetLastError());
     if (!check) return 0;
     // queries whose estimated error is above the threshold: plain FP32 form
