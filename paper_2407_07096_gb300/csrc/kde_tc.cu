@@ -468,11 +468,13 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
             for (int64_t t = t0; t < t1; ++t, ++tcount) {
                 const int acc = tcount & 1;
                 const int ms = tcount % SMETA;
-                // every lane waits; the outcome is made warp-uniform so that the warp never
-                // splits around the __syncwarp calls below
-                bool got = ptx::mbar_wait_bounded(&acc_full[acc], (tcount >> 1) & 1, kWaitLimitNs, abort_flag) &&
-                           ptx::mbar_wait_bounded(&full_m[ms], (tcount / SMETA) & 1, kWaitLimitNs, abort_flag);
-                if (!__all_sync(0xffffffffu, got)) {
+                // lane 0 waits (the other lanes do not spend issue slots polling); the
+                // outcome is broadcast so that the warp never splits around __syncwarp
+                bool got = true;
+                if (lane == 0)
+                    got = ptx::mbar_wait_bounded(&acc_full[acc], (tcount >> 1) & 1, kWaitLimitNs, abort_flag) &&
+                          ptx::mbar_wait_bounded(&full_m[ms], (tcount / SMETA) & 1, kWaitLimitNs, abort_flag);
+                if (!__shfl_sync(0xffffffffu, (int)got, 0)) {
                     timed_out();
                     ok = false;
                     break;
