@@ -185,31 +185,42 @@ EX2_PER_SM_CLK = 32.0         # MUFU ex2 results per SM per clock (measured by t
 SMS = 152
 
 
+def _kp(d):
+    for kp in (16, 32, 64, 128):
+        if d <= kp:
+            return kp
+    return None
+
+
 def roofline_for(form, d, pairs, ms, clocks, peaks):
-    """Roofline object for the dominant (pairwise) kernel."""
+    """Roofline object for the dominant (pairwise) kernel, per launch."""
     f_hz = (clocks.get("sm_mhz") or 1900.0) * 1e6
     sec = ms * 1e-3
+    ex2_peak = EX2_PER_SM_CLK * SMS * f_hz
+    tensor_peak = peaks["bf16_tflops"] * 1e12
+    # the path's roofline: the slower of 2mnd tensor flops and one ex2 per pair
+    t_ns = max(2.0 * d * pairs / tensor_peak, pairs / ex2_peak)
     if form in ("simt_f32", "simt_f64"):
         d_pad = 4 * math.ceil(d / 4)
         ops = pairs * (2 * d_pad + 3)  # FSUB + FFMA per coordinate; FFMA, ex2, FADD per pair
         peak = FP32_LANES_PER_SM * SMS * f_hz
         return {"bound": "alu", "achieved": ops / sec / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                "frac": ops / sec / peak, "traffic": None,
+                "frac": ops / sec / peak, "traffic": None, "path_roofline_frac": t_ns / sec,
                 "note": f"FP32 pipe: (2*{d_pad}+3) ops/pair vs 128 lanes x {SMS} SMs x sampled clock"}
-    # tensor-core form: the slower of the tensor pipe (3 split-FP16 products) and MUFU ex2
-    k_pad = 16 * math.ceil(d / 16)
-    flops = pairs * 2 * 3 * k_pad
-    t_tensor = flops / (peaks["bf16_tflops"] * 1e12)
-    ex2_peak = EX2_PER_SM_CLK * SMS * f_hz
+    # tensor-core form: 3 split-FP16 products over K = Kp plus one K = 16 step (point term)
+    kp = _kp(d)
+    flops = pairs * 2 * (3 * kp + 16)
+    t_tensor = flops / tensor_peak
     t_mufu = pairs / ex2_peak
+    common = {"traffic": None, "path_roofline_frac": t_ns / sec,
+              "tensor_frac": flops / sec / tensor_peak, "mufu_frac": pairs / sec / ex2_peak}
     if t_mufu >= t_tensor:
         return {"bound": "alu", "achieved": pairs / sec / 1e12, "peak": ex2_peak / 1e12, "unit": "Tex2/s",
-                "frac": pairs / sec / ex2_peak, "traffic": None,
-                "tensor_frac": flops / sec / (peaks["bf16_tflops"] * 1e12),
-                "note": "MUFU ex2 bound: one ex2 per pair"}
+                "frac": pairs / sec / ex2_peak, **common,
+                "note": "MUFU ex2 bound: one ex2 per pair (32 per SM per clock x sampled clock)"}
     return {"bound": "tensor", "achieved": flops / sec / 1e12, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-            "frac": flops / sec / (peaks["bf16_tflops"] * 1e12), "traffic": None,
-            "note": "3 split-FP16 products over K=pad16(d)"}
+            "frac": flops / sec / tensor_peak, **common,
+            "note": f"form flops 2*(3*{kp}+16) per pair vs measured dense FP16/bf16 peak"}
 
 
 def run_gpu(args):
@@ -277,6 +288,7 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
     prof = [k.profile_end() for k in kdes]
+    recomputed = [k.last_recomputed() for k in kdes]
     kern_ms = sum(p[0] for p in prof)
     kern_launches = sum(p[1] for p in prof)
     kern_pairs = sum(p[2] for p in prof)
@@ -327,6 +339,7 @@ def run_gpu(args):
                            "form": form, "l2": "flushed between steps (512 MiB write)",
                            "parallelism": f"replicas x{world} (query batches)"},
                 "create_ms": create_ms, "gpu_launches": int(launches), "roofline": roof,
+                "recomputed_fp32_queries": recomputed,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}
         print(json.dumps(line), flush=True)
