@@ -107,6 +107,33 @@ int stag_kde_query(stag_kde_t *h, const void *Q, int64_t m, double *out);
  */
 int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, void *stream);
 
+/*
+ * Batched evaluation: instance i evaluates the device query matrix dQs[i] (ms[i] rows,
+ * the handle's element type and d) against handle hs[i] into dOuts[i] (ms[i] doubles).
+ * The handles must be distinct and live on one device; ms[i] may differ, and so may the
+ * handles' n, d and a. Tensor-core instances of the same operand width share ONE
+ * persistent kernel launch whose work list spans all their (query tile, point range)
+ * units; every instance keeps its own partial sums and FP64 combine, so its results
+ * equal a solo call on the same handle within the form's tolerance.
+ * The first call with a given (handles, pointers, sizes) tunes the tensor-core launch
+ * settings on the batch, reserves all scratch and captures the whole batch into a CUDA
+ * graph (it synchronises the device and must not be made while a stream capture is in
+ * progress); later calls with the same arguments replay the graph on `stream` without
+ * allocating. A handle's later query of larger m (scratch growth) or destruction
+ * invalidates the cached graph (it is rebuilt on the next call). Work is asynchronous:
+ * results are valid once `stream` reaches this point. STAG_KDE_ETIMEDOUT reports a
+ * bounded wait that expired during the previous replay of the same batch.
+ */
+int stag_kde_query_batch(stag_kde_t *const *hs, const void *const *dQs, const int64_t *ms,
+                         double *const *dOuts, int64_t count, void *stream);
+
+/*
+ * Times the tensor-core form's launch settings (epilogue warp groups, point tiles per
+ * work unit) on the given device query batch and keeps the fastest for this handle's
+ * later queries. No-op for other forms. Synchronises; allocates a temporary output.
+ */
+int stag_kde_autotune(stag_kde_t *h, const void *dQ, int64_t m);
+
 /* Pre-sizes the handle's scratch for queries of up to m rows. */
 int stag_kde_reserve(stag_kde_t *h, int64_t m);
 

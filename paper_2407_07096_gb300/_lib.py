@@ -42,6 +42,9 @@ SIGNATURES = [
     ("stag_kde_query", _INT, [_VP, _VP, _I64, _VP]),
     ("stag_kde_query_dev", _INT, [_VP, _VP, _I64, _VP, _VP]),
     ("stag_kde_reserve", _INT, [_VP, _I64]),
+    ("stag_kde_query_batch", _INT, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_I64),
+                                    ctypes.POINTER(_VP), _I64, _VP]),
+    ("stag_kde_autotune", _INT, [_VP, _VP, _I64]),
     ("stag_kde_info", _INT, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_DBL),
                              ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     ("stag_kde_destroy", None, [_VP]),

@@ -34,6 +34,7 @@ constexpr int kSimtKC = 32;    // coordinates per shared-memory chunk
 
 // Process-wide count of kernel launches (reported by stag_kde_launch_count).
 void count_launch(int k = 1);
+void uncount_launches(uint64_t k);
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
@@ -58,6 +59,9 @@ struct stag_kde {
     int form = STAG_KDE_FORM_SIMT_F32;
     int normalise = 0;
     bool tc_check = true;  // recompute queries the tensor-core error estimate flags
+    uint64_t scratch_epoch = 0;    // bumped whenever scratch is reallocated (graphs hold pointers)
+    int tune_eg = 0;               // tensor-core epilogue warp groups (0 = default)
+    int tune_tiles_per_unit = 0;   // point tiles per work unit (0 = heuristic)
     cudaStream_t stream = nullptr;  // the handle's own stream (host API)
 
     // plain FP32 form: tile-transposed points
@@ -104,6 +108,8 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
 int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaStream_t s,
                    int *dflag);
 int ensure_partials(stag_kde *h, int64_t entries);
+// Sizes the plain form's scratch (tiled queries, partials) for queries of up to m rows.
+int simt_reserve(stag_kde *h, int64_t m);
 // Recomputes with the plain FP32 form the rows idx[0 .. *count) of dQ (device count)
 // and writes their densities to dOut[idx[j]].
 int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
@@ -125,6 +131,19 @@ int tc_prepare_points(stag_kde *h, const float *dX);
 int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag);
 void tc_free(stag_kde *h);
 int tc_check_error(stag_kde *h, cudaStream_t s);
+int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit);
+// Pieces of a tensor-core query for the batched path (kde_tc.cu).
+int tc_operand_width(const stag_kde *h);
+int tc_epilogue_groups();
+size_t tc_inst_size();
+int tc_prep_public(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s);
+int64_t tc_fill_inst(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t unit_begin, void *inst,
+                     int64_t *splits);
+int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total_units, int *err, int sm_count,
+                    cudaStream_t s);
+int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s);
+// kde_batch.cu
+void batch_forget_handle(stag_kde *h);
 int tc_fixed_rows(stag_kde *h, int64_t *count);
 bool tc_supported(int64_t d);
 

@@ -328,6 +328,7 @@ int grid_for(int64_t total, int threads) {
 
 int ensure_partials(stag_kde *h, int64_t entries) {
     if (h->part.cap >= entries) return 0;
+    ++h->scratch_epoch;
     if (h->part.sum) cudaFree(h->part.sum);
     if (h->part.shift) cudaFree(h->part.shift);
     h->part = Partials{};
@@ -339,6 +340,7 @@ int ensure_partials(stag_kde *h, int64_t entries) {
 
 int ensure_qt(stag_kde *h, int64_t floats) {
     if (h->qt_cap >= floats) return 0;
+    ++h->scratch_epoch;
     if (h->qt) cudaFree(h->qt);
     h->qt = nullptr;
     h->qt_cap = 0;
@@ -417,6 +419,14 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
     STAG_CUDA_TRY(cudaGetLastError());
     return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
                           dOut, s);
+}
+
+int simt_reserve(stag_kde *h, int64_t m) {
+    const int64_t q_tiles = ceil_div(m, kSimtTile);
+    int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
+    if (rc) return rc;
+    const int64_t tps = choose_tiles_per_split(h, q_tiles);
+    return ensure_partials(h, ceil_div(h->n_tiles, tps) * m);
 }
 
 int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,

@@ -97,6 +97,8 @@ constexpr int BM = 128;  // queries per tile (MMA M, TMEM lanes)
 // FP32 form; the estimate bounds the measured error from above (ratio <= ~0.96), so the
 // queries kept stay below ~7.2e-5 against the 1e-4 tolerance.
 constexpr double kTcErrThreshold = 7.5e-5;
+}  // namespace
+
 // Epilogue warps per TMEM lane quadrant (2 or 4); STAG_KDE_TC_EG overrides the default.
 int tc_epilogue_groups() {
     static int eg = []() {
@@ -106,6 +108,8 @@ int tc_epilogue_groups() {
     }();
     return eg;
 }
+
+namespace {
 
 // ------------------------------------------------------------------ layout helpers
 template <int KP>
@@ -147,17 +151,34 @@ struct Cfg {
                   "planes must keep 1024-byte alignment");
 };
 
-struct TcParams {
+// One KDE instance as the tensor-core kernel sees it. A launch processes a table of
+// instances of the same operand width; the units of instance i are the global unit
+// indices [unit_begin, unit_begin + q_tiles * splits). The tensor maps sit in this
+// struct, in kernel-parameter space (one instance) or global memory (a batch table).
+struct alignas(64) TcInst {
+    CUtensorMap map_ahi, map_alo, map_aaug, map_bhi, map_blo, map_baug;
     const float *tinfo;    // [T][4]
     const float *rowterm;  // [T][m_pad]
     const float *scales;   // device: scale_v, scale_u, kk, s_a
     const unsigned *ub;    // [m_pad]: per-query upper bound on every exponent (order bits)
-    double *part_sum;
+    double *part_sum;      // [splits][m]
     float *part_shift;
     double *part_w;
-    int *err;
-    int64_t m, m_pad, n, T, q_tiles, tiles_per_split, units;
+    int64_t m, m_pad, n, T, q_tiles, tiles_per_split, unit_begin, units;
 };
+
+// The instance owning global unit u (binary search over unit_begin).
+__device__ __forceinline__ const TcInst *find_inst(const TcInst *insts, int n_inst, int64_t u) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (insts[mid].unit_begin <= u)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return insts + lo;
+}
 
 __device__ __forceinline__ int cexp(float e) { return (int)fminf(fmaxf(e, -4000.f), 4000.f); }
 
@@ -235,10 +256,9 @@ __device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32],
 
 template <int KP, int BN, int SB, int SMETA, int AB, int EG>
 __global__ void __launch_bounds__(64 + 128 * EG, 1) __maxnreg__(EG >= 4 ? 112 : 200)
-kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant__ CUtensorMap map_alo,
-              const __grid_constant__ CUtensorMap map_aaug, const __grid_constant__ CUtensorMap map_bhi,
-              const __grid_constant__ CUtensorMap map_blo, const __grid_constant__ CUtensorMap map_baug,
-              const TcParams p) {
+kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ table, int n_inst,
+              int64_t total_units, int *err) {
+    const TcInst *insts = table ? table : &inst0;
     using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
     using G = Geo<KP>;
     extern __shared__ uint8_t smem_raw[];
@@ -286,12 +306,14 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
         ptx::fence_proxy_async();
     }
     if (warp == 0 && lane == 0) {
-        ptx::prefetch_tensormap(&map_ahi);
-        ptx::prefetch_tensormap(&map_alo);
-        ptx::prefetch_tensormap(&map_aaug);
-        ptx::prefetch_tensormap(&map_bhi);
-        ptx::prefetch_tensormap(&map_blo);
-        ptx::prefetch_tensormap(&map_baug);
+        if (!table) {
+            ptx::prefetch_tensormap(&inst0.map_ahi);
+            ptx::prefetch_tensormap(&inst0.map_alo);
+            ptx::prefetch_tensormap(&inst0.map_aaug);
+            ptx::prefetch_tensormap(&inst0.map_bhi);
+            ptx::prefetch_tensormap(&inst0.map_blo);
+            ptx::prefetch_tensormap(&inst0.map_baug);
+        }
     }
     if (warp == 1) {
         ptx::tmem_alloc(tmem_holder, C::TMEM_COLS);
@@ -303,7 +325,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
     const uint32_t tmem_base = *tmem_holder;
 
     auto timed_out = [&]() {
-        atomicExch(p.err, kErrTimeout);
+        atomicExch(err, kErrTimeout);
         *abort_flag = 1;
     };
 
@@ -313,10 +335,12 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
             uint32_t ucount = 0, tcount = 0;
             uint32_t issued_a = 0, issued_b = 0, issued_m = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
-                const int64_t split = u / p.q_tiles, qt = u % p.q_tiles;
-                const int64_t t0 = split * p.tiles_per_split;
-                const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
+            for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++ucount) {
+                const TcInst &I = *find_inst(insts, n_inst, u);
+                const int64_t lu = u - I.unit_begin;
+                const int64_t split = lu / I.q_tiles, qt = lu % I.q_tiles;
+                const int64_t t0 = split * I.tiles_per_split;
+                const int64_t t1 = min(I.T, t0 + I.tiles_per_split);
                 const int ab = ucount % AB;
                 if (!ptx::mbar_wait_bounded(&a_empty[ab], ((ucount / AB) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
                     timed_out();
@@ -327,11 +351,11 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                 ptx::mbar_arrive_expect_tx(&a_full[ab], C::A_BYTES);
 #pragma unroll
                 for (int ch = 0; ch < G::CH; ++ch) {
-                    ptx::tma_load_2d(abuf + ch * BM * G::CW * 2, &map_ahi, ch * G::CW, (int)(qt * BM), &a_full[ab]);
-                    ptx::tma_load_2d(abuf + C::A_PLANE + ch * BM * G::CW * 2, &map_alo, ch * G::CW, (int)(qt * BM),
+                    ptx::tma_load_2d(abuf + ch * BM * G::CW * 2, &I.map_ahi, ch * G::CW, (int)(qt * BM), &a_full[ab]);
+                    ptx::tma_load_2d(abuf + C::A_PLANE + ch * BM * G::CW * 2, &I.map_alo, ch * G::CW, (int)(qt * BM),
                                      &a_full[ab]);
                 }
-                ptx::tma_load_2d(abuf + 2 * C::A_PLANE, &map_aaug, 0, 0, &a_full[ab]);
+                ptx::tma_load_2d(abuf + 2 * C::A_PLANE, &I.map_aaug, 0, 0, &a_full[ab]);
                 ++issued_a;
                 for (int64_t t = t0; t < t1; ++t, ++tcount) {
                     const int sb = tcount % SB;
@@ -344,11 +368,11 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     ptx::mbar_arrive_expect_tx(&full_b[sb], C::B_BYTES);
 #pragma unroll
                     for (int ch = 0; ch < G::CH; ++ch) {
-                        ptx::tma_load_2d(bbuf + ch * BN * G::CW * 2, &map_bhi, ch * G::CW, (int)(t * BN), &full_b[sb]);
-                        ptx::tma_load_2d(bbuf + C::B_PLANE + ch * BN * G::CW * 2, &map_blo, ch * G::CW, (int)(t * BN),
+                        ptx::tma_load_2d(bbuf + ch * BN * G::CW * 2, &I.map_bhi, ch * G::CW, (int)(t * BN), &full_b[sb]);
+                        ptx::tma_load_2d(bbuf + C::B_PLANE + ch * BN * G::CW * 2, &I.map_blo, ch * G::CW, (int)(t * BN),
                                          &full_b[sb]);
                     }
-                    ptx::tma_load_2d(bbuf + 2 * C::B_PLANE, &map_baug, 0, (int)(t * BN), &full_b[sb]);
+                    ptx::tma_load_2d(bbuf + 2 * C::B_PLANE, &I.map_baug, 0, (int)(t * BN), &full_b[sb]);
                     ++issued_b;
                     const int ms = tcount % SMETA;
                     if (!ptx::mbar_wait_bounded(&empty_m[ms], ((tcount / SMETA) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
@@ -358,8 +382,8 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     }
                     uint8_t *mbuf = smem + C::OFF_META + ms * C::META_STRIDE;
                     ptx::mbar_arrive_expect_tx(&full_m[ms], C::META_BYTES);
-                    ptx::bulk_load(mbuf, p.rowterm + t * p.m_pad + qt * BM, BM * 4, &full_m[ms]);
-                    ptx::bulk_load(mbuf + BM * 4, p.tinfo + t * 4, 16, &full_m[ms]);
+                    ptx::bulk_load(mbuf, I.rowterm + t * I.m_pad + qt * BM, BM * 4, &full_m[ms]);
+                    ptx::bulk_load(mbuf + BM * 4, I.tinfo + t * 4, 16, &full_m[ms]);
                     ++issued_m;
                 }
             }
@@ -385,10 +409,11 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
             bool ok = true;
             const uint32_t a0 = ptx::smem_u32(smem + C::OFF_A);
             const uint32_t b0 = ptx::smem_u32(smem + C::OFF_B);
-            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++ucount) {
-                const int64_t split = u / p.q_tiles;
-                const int64_t t0 = split * p.tiles_per_split;
-                const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
+            for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++ucount) {
+                const TcInst &I = *find_inst(insts, n_inst, u);
+                const int64_t split = (u - I.unit_begin) / I.q_tiles;
+                const int64_t t0 = split * I.tiles_per_split;
+                const int64_t t1 = min(I.T, t0 + I.tiles_per_split);
                 const int ab = ucount % AB;
                 if (!ptx::mbar_wait_bounded(&a_full[ab], (ucount / AB) & 1, kWaitLimitNs, abort_flag)) {
                     timed_out();
@@ -452,18 +477,20 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
         constexpr int COLS = BN / EG;
         constexpr int NCH = COLS / 32;
         static_assert(COLS % 32 == 0, "column group must be whole 32-column chunks");
-        const float kk = p.scales[2];
         double *msum = reinterpret_cast<double *>(smem + C::OFF_MERGE);   // [EG-1][BM]
         double *mw = msum + (EG - 1) * BM;                                 // [EG-1][BM]
         float *mshift = reinterpret_cast<float *>(mw + (EG - 1) * BM);     // [EG-1][BM]
         uint32_t tcount = 0, ucount = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
-            const int64_t split = u / p.q_tiles, qt = u % p.q_tiles;
-            const int64_t t0 = split * p.tiles_per_split;
-            const int64_t t1 = min(p.T, t0 + p.tiles_per_split);
+        for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+            const TcInst &I = *find_inst(insts, n_inst, u);
+            const int64_t lu = u - I.unit_begin;
+            const int64_t split = lu / I.q_tiles, qt = lu % I.q_tiles;
+            const int64_t t0 = split * I.tiles_per_split;
+            const int64_t t1 = min(I.T, t0 + I.tiles_per_split);
+            const float kk = I.scales[2];
             // the row's fixed shift: ceil of an upper bound on every exponent of the row
-            const float s_row = ceilf(order_bits_to_float(p.ub[qt * BM + row]));
+            const float s_row = ceilf(order_bits_to_float(I.ub[qt * BM + row]));
             RowState st{s_row, 0.f, 0.0, 0.f, 0.0};
             for (int64_t t = t0; t < t1; ++t, ++tcount) {
                 const int acc = tcount & 1;
@@ -485,7 +512,7 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                 const float vrad = meta[BM];
                 // real points among this warp's columns (only the last tile is padded)
                 const int64_t col0 = t * BN + grp * COLS;
-                const int vcols = (int)max((int64_t)0, min((int64_t)COLS, p.n - col0));
+                const int vcols = (int)max((int64_t)0, min((int64_t)COLS, I.n - col0));
                 const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS;
                 if constexpr (EG >= 4 || NCH == 1) {
                     // enough warps per scheduler to hide the TMEM load latency: one buffer
@@ -584,10 +611,10 @@ kde_tc_kernel(const __grid_constant__ CUtensorMap map_ahi, const __grid_constant
                     wt += ldexp(ow[g], e);
                 }
                 const int64_t q = qt * BM + row;
-                if (q < p.m) {
-                    p.part_sum[split * p.m + q] = tot;
-                    p.part_shift[split * p.m + q] = sm;
-                    p.part_w[split * p.m + q] = wt;
+                if (q < I.m) {
+                    I.part_sum[split * I.m + q] = tot;
+                    I.part_shift[split * I.m + q] = sm;
+                    I.part_w[split * I.m + q] = wt;
                 }
             }
             ++ucount;
@@ -915,22 +942,37 @@ int bn_for(int Kp) { return Kp >= 128 ? 128 : 256; }
 int grid_for(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_div(total, threads), 152 * 16); }
 
 template <int KP, int BN, int SB, int SMETA, int AB, int EG>
-int launch_tc(stag_kde *h, const TcParams &prm, cudaStream_t s) {
+int launch_tc(const TcInst &inst0, const TcInst *table, int n_inst, int64_t total_units, int *err, int sm_count,
+              cudaStream_t s) {
     using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
     auto kern = kde_tc_kernel<KP, BN, SB, SMETA, AB, EG>;
     static_assert(C::SMEM <= 232448, "shared memory budget");
     // at least 116 KB so that no two CTAs share an SM (each holds up to 512 TMEM columns)
     const int smem = std::max(C::SMEM, 118 * 1024);
-    STAG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const int grid = (int)std::min<int64_t>(prm.units, h->sm_count);
-    TcData *tc = h->tc;
+    // set once per instantiation (before any stream capture can be in progress)
+    static cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    STAG_CUDA_TRY(attr);
+    const int grid = (int)std::min<int64_t>(total_units, sm_count);
     count_launch();
-    prof_start(h, s);
-    kern<<<grid, C::THREADS, smem, s>>>(tc->map_ahi, tc->map_alo, tc->map_aaug, tc->map_bhi, tc->map_blo,
-                                        tc->map_baug, prm);
-    prof_stop(h, s, (double)prm.m * (double)h->n);
+    kern<<<grid, C::THREADS, smem, s>>>(inst0, table, n_inst, total_units, err);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
+}
+
+// Dispatch on the operand width and the number of epilogue warp groups.
+int launch_tc_any(int Kp, int eg, const TcInst &inst0, const TcInst *table, int n_inst, int64_t total_units,
+                  int *err, int sm_count, cudaStream_t s) {
+    switch (Kp * 10 + eg) {
+        case 162: return launch_tc<16, 256, 4, 8, 2, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 164: return launch_tc<16, 256, 4, 8, 2, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 322: return launch_tc<32, 256, 4, 8, 2, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 324: return launch_tc<32, 256, 4, 8, 2, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 642: return launch_tc<64, 256, 2, 8, 1, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 644: return launch_tc<64, 256, 2, 8, 1, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 1282: return launch_tc<128, 128, 2, 8, 1, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 1284: return launch_tc<128, 128, 2, 8, 1, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
+    }
+    return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported operand width");
 }
 
 }  // namespace
@@ -1018,6 +1060,7 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
 static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
     TcData *tc = h->tc;
     const int Kp = tc->Kp;
+    if (tc->a_rows_cap < m_pad || tc->unorm_cap < m_pad || tc->rt_cap < tc->T * m_pad) ++h->scratch_epoch;
     if (tc->a_rows_cap < m_pad) {
         cudaFree(tc->a_hi);
         cudaFree(tc->a_lo);
@@ -1058,79 +1101,103 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
     return 0;
 }
 
-int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag) {
+// Work split of one query call: units of (query tile, range of point tiles). With
+// tiles_per_unit = 0 the ranges are chosen for ~8 units per SM; otherwise each range has
+// about tiles_per_unit tiles (the batched path uses this to even out unit sizes).
+static void plan_units(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t *q_tiles, int64_t *splits,
+                       int64_t *tps) {
+    const TcData *tc = h->tc;
+    const int64_t m_pad = round_up(m, BM);
+    *q_tiles = m_pad / BM;
+    int64_t sp;
+    if (tiles_per_unit > 0) {
+        sp = std::max<int64_t>(1, ceil_div(tc->T, tiles_per_unit));
+    } else {
+        sp = std::max<int64_t>(1, ceil_div((int64_t)h->sm_count * 8, *q_tiles));
+        sp = std::min<int64_t>(sp, std::max<int64_t>(1, tc->T / 4));
+    }
+    *tps = ceil_div(tc->T, sp);
+    *splits = ceil_div(tc->T, *tps);
+}
+
+int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit) {
+    TcData *tc = h->tc;
+    const int64_t m_pad = round_up(std::max<int64_t>(m, 1), BM);
+    int rc = ensure_query_scratch(h, m_pad);
+    if (rc) return rc;
+    int64_t qt, sp, tps;
+    plan_units(h, m, tiles_per_unit, &qt, &sp, &tps);
+    // the plain form's recompute path shares the partials buffer and needs its tiled copy
+    rc = simt_reserve(h, m);
+    if (rc) return rc;
+    rc = ensure_partials(h, sp * m);
+    if (rc) return rc;
+    if (tc->part_w_cap < sp * m) {
+        ++h->scratch_epoch;
+        cudaFree(tc->part_w);
+        tc->part_w = nullptr;
+        tc->part_w_cap = 0;
+        STAG_CUDA_TRY(cudaMalloc(&tc->part_w, sp * m * sizeof(double)));
+        tc->part_w_cap = sp * m;
+    }
+    return 0;
+}
+
+// Query-side preparation: FP16 splits of the queries, the row terms and bounds.
+static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     TcData *tc = h->tc;
     const int Kp = tc->Kp;
     const int64_t m_pad = round_up(m, BM);
-    int rc = ensure_query_scratch(h, m_pad);
-    if (rc) return rc;
-    if (dflag) {
-        rc = launch_check_finite_f32(dQ, m * h->d, dflag, s);
-        if (rc) return rc;
-    }
     const double c = h->a * 1.4426950408889634;
     STAG_CUDA_TRY(cudaMemsetAsync(tc->qbad, 0, m_pad * sizeof(int), s));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->ub, 0, m_pad * sizeof(unsigned), s));
     count_launch(2);
     tc_split_queries_kernel<<<grid_for(m_pad * Kp, 256), 256, 0, s>>>(dQ, m, h->d, Kp, m_pad, tc->cg, tc->scales,
                                                                       tc->a_hi, tc->a_lo, tc->qbad);
-    {
-        const int tpb = 64;
-        static std::once_flag attr_once;
-        std::call_once(attr_once, []() {
-            cudaFuncSetAttribute(tc_rowterm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4);
-        });
-        dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
-        tc_rowterm_kernel<<<grid, 128, Kp * 128 * sizeof(float), s>>>(dQ, m, h->d, Kp, m_pad, tc->cent, tc->T, tpb,
-                                                                      (float)c, tc->rowterm, tc->cg, tc->unorm,
-                                                                      tc->tinfo, tc->ub);
-    }
+    const int tpb = 64;
+    static std::once_flag attr_once;
+    std::call_once(attr_once, []() {
+        cudaFuncSetAttribute(tc_rowterm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4);
+    });
+    dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
+    tc_rowterm_kernel<<<grid, 128, Kp * 128 * sizeof(float), s>>>(dQ, m, h->d, Kp, m_pad, tc->cent, tc->T, tpb,
+                                                                  (float)c, tc->rowterm, tc->cg, tc->unorm, tc->tinfo,
+                                                                  tc->ub);
     STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
 
-    // work units: (query tile, range of point tiles), enough for ~8 per SM
-    const int64_t q_tiles = m_pad / BM;
-    int64_t splits = std::max<int64_t>(1, ceil_div((int64_t)h->sm_count * 8, q_tiles));
-    splits = std::min<int64_t>(splits, std::max<int64_t>(1, tc->T / 4));
-    const int64_t tps = ceil_div(tc->T, splits);
-    splits = ceil_div(tc->T, tps);
-    rc = ensure_partials(h, splits * m);
-    if (rc) return rc;
-    if (tc->part_w_cap < splits * m) {
-        cudaFree(tc->part_w);
-        tc->part_w = nullptr;
-        tc->part_w_cap = 0;
-        STAG_CUDA_TRY(cudaMalloc(&tc->part_w, splits * m * sizeof(double)));
-        tc->part_w_cap = splits * m;
-    }
-    TcParams prm;
-    prm.tinfo = tc->tinfo;
-    prm.rowterm = tc->rowterm;
-    prm.scales = tc->scales;
-    prm.ub = tc->ub;
-    prm.part_sum = h->part.sum;
-    prm.part_shift = h->part.shift;
-    prm.part_w = tc->part_w;
-    prm.err = tc->err;
-    prm.m = m;
-    prm.m_pad = m_pad;
-    prm.n = h->n;
-    prm.T = tc->T;
-    prm.q_tiles = q_tiles;
-    prm.tiles_per_split = tps;
-    prm.units = q_tiles * splits;
-    const int eg = tc_epilogue_groups();
-    switch (Kp * 10 + eg) {
-        case 162: rc = launch_tc<16, 256, 4, 8, 2, 2>(h, prm, s); break;
-        case 164: rc = launch_tc<16, 256, 4, 8, 2, 4>(h, prm, s); break;
-        case 322: rc = launch_tc<32, 256, 4, 8, 2, 2>(h, prm, s); break;
-        case 324: rc = launch_tc<32, 256, 4, 8, 2, 4>(h, prm, s); break;
-        case 642: rc = launch_tc<64, 256, 2, 8, 1, 2>(h, prm, s); break;
-        case 644: rc = launch_tc<64, 256, 2, 8, 1, 4>(h, prm, s); break;
-        case 1282: rc = launch_tc<128, 128, 2, 8, 1, 2>(h, prm, s); break;
-        case 1284: rc = launch_tc<128, 128, 2, 8, 1, 4>(h, prm, s); break;
-        default: return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported d");
-    }
-    if (rc) return rc;
+// Fills the kernel's view of one instance (units numbered from unit_begin).
+static void fill_inst(const stag_kde *h, int64_t m, int64_t q_tiles, int64_t splits, int64_t tps, int64_t unit_begin,
+                      TcInst *I) {
+    const TcData *tc = h->tc;
+    I->map_ahi = tc->map_ahi;
+    I->map_alo = tc->map_alo;
+    I->map_aaug = tc->map_aaug;
+    I->map_bhi = tc->map_bhi;
+    I->map_blo = tc->map_blo;
+    I->map_baug = tc->map_baug;
+    I->tinfo = tc->tinfo;
+    I->rowterm = tc->rowterm;
+    I->scales = tc->scales;
+    I->ub = tc->ub;
+    I->part_sum = h->part.sum;
+    I->part_shift = h->part.shift;
+    I->part_w = tc->part_w;
+    I->m = m;
+    I->m_pad = round_up(m, BM);
+    I->n = h->n;
+    I->T = tc->T;
+    I->q_tiles = q_tiles;
+    I->tiles_per_split = tps;
+    I->unit_begin = unit_begin;
+    I->units = q_tiles * splits;
+}
+
+// FP64 combine with the per-query error estimate, then the plain-form recompute of the
+// flagged queries.
+static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
+    TcData *tc = h->tc;
     const bool check = h->tc_check;
     if (check) STAG_CUDA_TRY(cudaMemsetAsync(tc->fix_count, 0, sizeof(int), s));
     count_launch();
@@ -1139,8 +1206,55 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
         tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
     STAG_CUDA_TRY(cudaGetLastError());
     if (!check) return 0;
-    // queries whose estimated error is above the threshold: plain FP32 form
     return simt_fixup_rows(h, dQ, m, tc->fix_idx, tc->fix_count, dOut, s);
+}
+
+int tc_operand_width(const stag_kde *h) { return h->tc ? h->tc->Kp : 0; }
+
+size_t tc_inst_size() { return sizeof(TcInst); }
+
+int tc_prep_public(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) { return tc_prep(h, dQ, m, s); }
+
+int64_t tc_fill_inst(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t unit_begin, void *inst,
+                     int64_t *splits) {
+    int64_t q_tiles, tps;
+    plan_units(h, m, tiles_per_unit, &q_tiles, splits, &tps);
+    TcInst *I = reinterpret_cast<TcInst *>(inst);
+    fill_inst(h, m, q_tiles, *splits, tps, unit_begin, I);
+    return I->units;
+}
+
+int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total_units, int *err, int sm_count,
+                    cudaStream_t s) {
+    static TcInst unused{};  // kernel parameter slot; the kernel reads the table
+    return launch_tc_any(Kp, eg, unused, reinterpret_cast<const TcInst *>(table), n_inst, total_units, err, sm_count,
+                         s);
+}
+
+int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
+    return tc_finish(h, dQ, m, splits, dOut, s);
+}
+
+int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag) {
+    TcData *tc = h->tc;
+    int rc = tc_reserve(h, m, h->tune_tiles_per_unit);
+    if (rc) return rc;
+    if (dflag) {
+        rc = launch_check_finite_f32(dQ, m * h->d, dflag, s);
+        if (rc) return rc;
+    }
+    rc = tc_prep(h, dQ, m, s);
+    if (rc) return rc;
+    int64_t q_tiles, splits, tps;
+    plan_units(h, m, h->tune_tiles_per_unit, &q_tiles, &splits, &tps);
+    TcInst inst;
+    fill_inst(h, m, q_tiles, splits, tps, 0, &inst);
+    prof_start(h, s);
+    rc = launch_tc_any(tc->Kp, h->tune_eg ? h->tune_eg : tc_epilogue_groups(), inst, nullptr, 1, inst.units,
+                       tc->err, h->sm_count, s);
+    prof_stop(h, s, (double)m * (double)h->n);
+    if (rc) return rc;
+    return tc_finish(h, dQ, m, splits, dOut, s);
 }
 
 int tc_fixed_rows(stag_kde *h, int64_t *count) {

@@ -21,6 +21,7 @@ static thread_local std::string g_last_error;
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
+void uncount_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
@@ -99,6 +100,7 @@ int check_a(double a) {
 
 void free_handle(stag_kde *h) {
     if (!h) return;
+    batch_forget_handle(h);
     DeviceGuard g(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     tc_free(h);
@@ -142,6 +144,7 @@ int resolve_form(int requested, int dtype, int64_t d, int *form) {
 
 int ensure_bytes(void **p, int64_t *cap, int64_t bytes) {
     if (*cap >= bytes) return 0;
+    // (callers bump the handle's scratch epoch)
     cudaFree(*p);
     *p = nullptr;
     *cap = 0;
@@ -275,11 +278,10 @@ int stag_kde_reserve(stag_kde_t *h, int64_t m) {
     int rc = ensure_bytes(&h->q_dev, &h->q_dev_cap, std::max<int64_t>(1, m * h->d) * elem_size(h->dtype));
     if (!rc) rc = ensure_bytes((void **)&h->out_dev, &h->out_cap, std::max<int64_t>(1, m) * 8);
     if (rc) return rc;
-    if (h->form == STAG_KDE_FORM_SIMT_F32 || h->form == STAG_KDE_FORM_TC) {
-        rc = ensure_qt(h, ceil_div(m, kSimtTile) * h->d_pad * kSimtTile);
-        if (rc) return rc;
-    }
-    return 0;
+    if (h->form == STAG_KDE_FORM_SIMT_F32) rc = simt_reserve(h, std::max<int64_t>(m, 1));
+    if (h->form == STAG_KDE_FORM_TC) rc = tc_reserve(h, std::max<int64_t>(m, 1), h->tune_tiles_per_unit);
+    if (h->form == STAG_KDE_FORM_SIMT_F64 && h->normalise) rc = ensure_partials(h, std::max<int64_t>(m, 1));
+    return rc;
 }
 
 int stag_kde_query(stag_kde_t *h, const void *Q, int64_t m, double *out) {

@@ -106,6 +106,10 @@ class ExactGaussianKDE:
         L.check(self._lib.stag_kde_profile_end(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)))
         return ms.value, n.value, pairs.value
 
+    def autotune(self, Q):
+        """Tunes the tensor-core launch settings on the CUDA query tensor Q."""
+        L.check(self._lib.stag_kde_autotune(self._h, Q.data_ptr(), Q.shape[0]))
+
     def reserve(self, m: int):
         L.check(self._lib.stag_kde_reserve(self._h, int(m)))
 
@@ -125,3 +129,21 @@ class ExactGaussianKDE:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def query_batch(kdes, Qs, outs=None, stream=None):
+    """Evaluates ``Qs[i]`` (contiguous CUDA tensors) against ``kdes[i]`` in one batched
+    call (one persistent tensor-core launch per operand width, replayed from a captured
+    CUDA graph on repeated calls with the same tensors). Returns the output tensors."""
+    import torch
+    lib = L.load()
+    n = len(kdes)
+    if outs is None:
+        outs = [torch.empty(q.shape[0], dtype=torch.float64, device=q.device) for q in Qs]
+    hs = (ctypes.c_void_p * n)(*[k._h.value for k in kdes])
+    qs = (ctypes.c_void_p * n)(*[q.data_ptr() for q in Qs])
+    ms = (ctypes.c_int64 * n)(*[q.shape[0] for q in Qs])
+    os_ = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    s = stream if stream is not None else torch.cuda.current_stream()
+    L.check(lib.stag_kde_query_batch(hs, qs, ms, os_, n, ctypes.c_void_p(s.cuda_stream)))
+    return outs
