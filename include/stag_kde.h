@@ -199,6 +199,58 @@ uint64_t stag_kde_launch_count(void);
 int stag_kde_eval_noalloc(const float *dX, int64_t n, const float *dQ, int64_t m, int64_t d, double a,
                           double *dOut, void *stream);
 
+/*
+ * Serving with continuous batching. The caller creates a handle per dataset (they stay
+ * resident) and starts a server over them; any thread may then submit query batches.
+ * A dispatcher thread merges pending requests for the same dataset, in arrival order, into
+ * launch groups of at most max_rows rows, admits a group when one of `slots` execution
+ * slots is free and the device memory of the groups in flight stays within
+ * mem_budget_bytes (a group larger than the budget runs alone), and runs groups of
+ * different slots concurrently (one CUDA stream per slot; each slot has its own scratch
+ * for every dataset). Requests arriving while others are on the GPU join the next
+ * groups. Results equal a solo stag_kde_query on the same handle within the form's
+ * tolerance.
+ */
+typedef struct stag_srv stag_srv_t;
+
+typedef struct stag_srv_opts {
+    stag_kde_t *const *datasets; /* handles (created by the caller, kept alive until stop) */
+    int n_datasets;
+    int slots;                   /* concurrent launch groups (default 4, at most 64)      */
+    int64_t max_rows;            /* rows per launch group and per request (default 8192) */
+    int64_t mem_budget_bytes;    /* device memory of the groups in flight (default 1 GiB)*/
+    int reserved[4];             /* must be zero                                         */
+} stag_srv_opts;
+
+void stag_srv_opts_init(stag_srv_opts *o);
+
+/* Starts the server: allocates the slots (streams, device and pinned staging buffers)
+ * and the dispatcher thread. Returns NULL on error (stag_kde_last_error()). */
+stag_srv_t *stag_srv_start(const stag_srv_opts *o);
+
+/* Queues Q (m x d host rows in the dataset's element type, 1 <= m <= max_rows) for
+ * dataset index `dataset`; out (m doubles, host) receives the densities. Q and out must
+ * stay valid until stag_srv_wait returns for *ticket. */
+int stag_srv_submit(stag_srv_t *s, int dataset, const void *Q, int64_t m, double *out, uint64_t *ticket);
+
+/* Waits for a request (timeout_us < 0: no limit). Returns 0 when out is filled,
+ * STAG_KDE_ETIMEDOUT if it did not finish in time (the ticket stays valid), or the
+ * request's error (STAG_KDE_ECANCELED for a cancelled request). A ticket is released
+ * by the wait that returns its final status. */
+int stag_srv_wait(stag_srv_t *s, uint64_t ticket, int64_t timeout_us);
+
+/* Cancels a request that has not been dispatched yet; its wait returns ECANCELED. */
+int stag_srv_cancel(stag_srv_t *s, uint64_t ticket);
+
+/* Completed requests, rows, and the median / 99th-percentile latency (submit to results
+ * copied out) in microseconds, since start or the last reset. */
+int stag_srv_stats(stag_srv_t *s, int64_t *completed, int64_t *rows, double *p50_us, double *p99_us);
+int stag_srv_reset_stats(stag_srv_t *s);
+
+/* Stops accepting requests, cancels those not yet dispatched, waits for the groups in
+ * flight and releases the server. No wait or submit may follow. NULL-safe. */
+int stag_srv_stop(stag_srv_t *s);
+
 #ifdef __cplusplus
 }
 #endif

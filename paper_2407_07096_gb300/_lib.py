@@ -28,6 +28,12 @@ class StagKdeError(RuntimeError):
         self.code = code
 
 
+class SrvOpts(ctypes.Structure):
+    _fields_ = [("datasets", ctypes.POINTER(ctypes.c_void_p)), ("n_datasets", ctypes.c_int),
+                ("slots", ctypes.c_int), ("max_rows", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
+                ("reserved", ctypes.c_int * 4)]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("normalise", ctypes.c_int), ("device", ctypes.c_int),
                 ("tc_no_check", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
@@ -53,6 +59,15 @@ SIGNATURES = [
     ("stag_kde_version", ctypes.c_char_p, []),
     ("stag_kde_launch_count", ctypes.c_uint64, []),
     ("stag_kde_profile_begin", _INT, [_VP]),
+    ("stag_srv_opts_init", None, [ctypes.POINTER(SrvOpts)]),
+    ("stag_srv_start", _VP, [ctypes.POINTER(SrvOpts)]),
+    ("stag_srv_submit", _INT, [_VP, _INT, _VP, _I64, _VP, ctypes.POINTER(ctypes.c_uint64)]),
+    ("stag_srv_wait", _INT, [_VP, ctypes.c_uint64, _I64]),
+    ("stag_srv_cancel", _INT, [_VP, ctypes.c_uint64]),
+    ("stag_srv_stats", _INT, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_DBL),
+                              ctypes.POINTER(_DBL)]),
+    ("stag_srv_reset_stats", _INT, [_VP]),
+    ("stag_srv_stop", _INT, [_VP]),
     ("stag_kde_eval_noalloc", _INT, [_VP, _I64, _VP, _I64, _I64, _DBL, _VP, _VP]),
     ("stag_kde_profile_end", _INT, [_VP, ctypes.POINTER(_DBL), ctypes.POINTER(_I64), ctypes.POINTER(_DBL)]),
 ]

@@ -60,6 +60,7 @@ struct stag_kde {
     int normalise = 0;
     bool tc_check = true;  // recompute queries the tensor-core error estimate flags
     uint64_t scratch_epoch = 0;    // bumped whenever scratch is reallocated (graphs hold pointers)
+    bool is_view = false;          // shares another handle's point-set data (serving slots)
     int tune_eg = 0;               // tensor-core epilogue warp groups (0 = default)
     int tune_tiles_per_unit = 0;   // point tiles per work unit (0 = heuristic)
     cudaStream_t stream = nullptr;  // the handle's own stream (host API)
@@ -132,6 +133,7 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
 void tc_free(stag_kde *h);
 int tc_check_error(stag_kde *h, cudaStream_t s);
 int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit);
+int tc_make_view(const stag_kde *base, stag_kde *view);
 // Pieces of a tensor-core query for the batched path (kde_tc.cu).
 int tc_operand_width(const stag_kde *h);
 int tc_epilogue_groups();
@@ -144,6 +146,10 @@ int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total
 int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s);
 // kde_batch.cu
 void batch_forget_handle(stag_kde *h);
+
+// stag_kde_api.cu: views (same point set, separate scratch) and their release
+stag_kde *make_view(stag_kde *base);
+void free_view(stag_kde *view);
 int tc_fixed_rows(stag_kde *h, int64_t *count);
 bool tc_supported(int64_t d);
 

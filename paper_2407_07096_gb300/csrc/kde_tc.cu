@@ -984,17 +984,21 @@ int tc_tile_points(int64_t d) { return kp_for(d) ? bn_for(kp_for(d)) : 0; }
 void tc_free(stag_kde *h) {
     TcData *tc = h->tc;
     if (!tc) return;
-    cudaFree(tc->b_hi);
-    cudaFree(tc->b_lo);
-    cudaFree(tc->b_aug);
-    cudaFree(tc->a_aug);
-    cudaFree(tc->tinfo);
-    cudaFree(tc->cent);
-    cudaFree(tc->cg);
-    cudaFree(tc->tsum);
-    cudaFree(tc->vmax_bits);
-    cudaFree(tc->xmax_bits);
-    cudaFree(tc->scales);
+    if (!h->is_view) {
+        // the point set's data (shared with views)
+        cudaFree(tc->b_hi);
+        cudaFree(tc->b_lo);
+        cudaFree(tc->b_aug);
+        cudaFree(tc->a_aug);
+        cudaFree(tc->tinfo);
+        cudaFree(tc->cent);
+        cudaFree(tc->cg);
+        cudaFree(tc->tsum);
+        cudaFree(tc->vmax_bits);
+        cudaFree(tc->xmax_bits);
+        cudaFree(tc->scales);
+    }
+    // per-handle scratch
     cudaFree(tc->a_hi);
     cudaFree(tc->a_lo);
     cudaFree(tc->rowterm);
@@ -1008,6 +1012,39 @@ void tc_free(stag_kde *h) {
     if (tc->err_host) cudaFreeHost(tc->err_host);
     delete tc;
     h->tc = nullptr;
+}
+
+// A view of the tensor-core data of `base`: shares the point set's arrays and tensor
+// maps, owns empty scratch of its own.
+int tc_make_view(const stag_kde *base, stag_kde *view) {
+    const TcData *b = base->tc;
+    if (!b) return 0;
+    TcData *tc = new (std::nothrow) TcData();
+    if (!tc) return fail(STAG_KDE_ENOMEM, "out of host memory");
+    view->tc = tc;
+    tc->Kp = b->Kp;
+    tc->BN = b->BN;
+    tc->T = b->T;
+    tc->n_pad = b->n_pad;
+    tc->b_hi = b->b_hi;
+    tc->b_lo = b->b_lo;
+    tc->b_aug = b->b_aug;
+    tc->a_aug = b->a_aug;
+    tc->tinfo = b->tinfo;
+    tc->cent = b->cent;
+    tc->cg = b->cg;
+    tc->tsum = b->tsum;
+    tc->vmax_bits = b->vmax_bits;
+    tc->xmax_bits = b->xmax_bits;
+    tc->scales = b->scales;
+    tc->map_bhi = b->map_bhi;
+    tc->map_blo = b->map_blo;
+    tc->map_baug = b->map_baug;
+    tc->map_aaug = b->map_aaug;
+    STAG_CUDA_TRY(cudaMalloc(&tc->err, sizeof(int)));
+    STAG_CUDA_TRY(cudaMemset(tc->err, 0, sizeof(int)));
+    STAG_CUDA_TRY(cudaMallocHost(&tc->err_host, sizeof(int)));
+    return 0;
 }
 
 int tc_prepare_points(stag_kde *h, const float *dX) {

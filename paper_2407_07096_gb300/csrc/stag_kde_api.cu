@@ -104,8 +104,10 @@ void free_handle(stag_kde *h) {
     DeviceGuard g(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     tc_free(h);
-    cudaFree(h->xt);
-    cudaFree(h->x64);
+    if (!h->is_view) {
+        cudaFree(h->xt);
+        cudaFree(h->x64);
+    }
     cudaFree(h->q_dev);
     cudaFree(h->qt);
     cudaFree(h->out_dev);
@@ -118,6 +120,47 @@ void free_handle(stag_kde *h) {
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
+
+}  // namespace
+
+stag_kde *make_view(stag_kde *base) {
+    stag_kde *v = new (std::nothrow) stag_kde();
+    if (!v) return (set_error("out of host memory"), nullptr);
+    DeviceGuard g(base->device);
+    v->device = base->device;
+    v->n = base->n;
+    v->d = base->d;
+    v->a = base->a;
+    v->dtype = base->dtype;
+    v->form = base->form;
+    v->normalise = base->normalise;
+    v->tc_check = base->tc_check;
+    v->tune_eg = base->tune_eg;
+    v->tune_tiles_per_unit = base->tune_tiles_per_unit;
+    v->is_view = true;
+    v->xt = base->xt;
+    v->n_tiles = base->n_tiles;
+    v->d_pad = base->d_pad;
+    v->x64 = base->x64;
+    v->sm_count = base->sm_count;
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMalloc(&v->flag_dev, sizeof(int))) != cudaSuccess ||
+        (e = cudaMallocHost(&v->flag_host, sizeof(int))) != cudaSuccess) {
+        cuda_fail(e, "view set-up");
+        free_handle(v);
+        return nullptr;
+    }
+    if (tc_make_view(base, v)) {
+        free_handle(v);
+        return nullptr;
+    }
+    return v;
+}
+
+void free_view(stag_kde *view) { free_handle(view); }
+
+namespace {
 
 int resolve_form(int requested, int dtype, int64_t d, int *form) {
     if (dtype == STAG_KDE_F64) {
