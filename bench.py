@@ -44,6 +44,8 @@ WORKLOADS = {
     # name: (description, builder)
     "single_d16": "exact Gaussian KDE n=m=100000 d=16 FP32, 10-component mixture means U[-10,10]^16 std 1, a in {0.01,0.1,1.0}",
     "large_d64": "exact Gaussian KDE n=2000000 m=100000 d=64 FP32, 50-component mixture means U[-10,10]^64 std logU[0.5,2], a=0.05",
+    "batched": "256 KDE instances, n logU[1000,200000], m logU[64,8192], d in {8,32,128}, a U[0.01,1], 10-component mixtures means U[-10,10]^d std 1, one batched call per step (graph replay)",
+    "serving": "8 resident datasets n log-spaced 1e4..2e6, d in {2,4,8,16,32,64,96,128}, a=1/d; Poisson arrivals, m logU[1,4096], random dataset; loads 0.3/0.6/0.9 x saturation",
 }
 
 
@@ -141,7 +143,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    X, Q, alist = build_workload(args.workload)
+    if args.workload in ("batched", "serving"):
+        # a bounded sample: the first instances of the batched workload
+        inst = build_batched(6)
+        X, Q, a0 = max(inst, key=lambda t: t[0].shape[0])
+        alist = [a0]
+    else:
+        X, Q, alist = build_workload(args.workload)
     threads = os.cpu_count() or 1
     # size each step so that warmup + steps stay within a few minutes
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
@@ -350,6 +358,178 @@ def run_gpu(args):
     return 0
 
 
+def build_batched(count=256, seed=0):
+    n_s = G.log_uniform_int(seed, 11, count, 1000, 200000)
+    m_s = G.log_uniform_int(seed, 12, count, 64, 8192)
+    a_s = 0.01 + 0.99 * G.uniform(seed, 13, count)
+    dims = (8, 32, 128)
+    inst = []
+    for i in range(count):
+        d = dims[i % 3]
+        mix = G.make_mixture(seed + i, 10, d, -10.0, 10.0, 1.0)
+        inst.append((G.sample(mix, seed + i, int(n_s[i]), "data"), G.sample(mix, seed + i, int(m_s[i]), "query"),
+                     float(a_s[i])))
+    return inst
+
+
+def run_batched(args):
+    import torch
+    from paper_2407_07096_gb300 import build as B
+    from paper_2407_07096_gb300 import _lib as L
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE, query_batch
+    B.build()
+    lib = L.load()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    inst = build_batched(args.count)
+    gen_s = time.perf_counter() - t0
+    kdes = [ExactGaussianKDE(X, a, form=args.form) for X, _, a in inst]
+    Qs = [torch.from_numpy(Q).to(dev) for _, Q, _ in inst]
+    outs = [torch.empty(q.shape[0], dtype=torch.float64, device=dev) for q in Qs]
+    pairs = float(sum(X.shape[0] * Q.shape[0] for X, Q, _ in inst))
+    stream = torch.cuda.Stream(dev)
+    t = time.perf_counter()
+    query_batch(kdes, Qs, outs, stream)  # plan: tune + capture
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t
+    for _ in range(args.warmup):
+        query_batch(kdes, Qs, outs, stream)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(0)
+    clocks.start()
+    l0 = lib.stag_kde_launch_count()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[i][0].record(stream)
+            query_batch(kdes, Qs, outs, stream)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lib.stag_kde_launch_count() - l0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    # parity on sampled queries of a few instances
+    import oracle
+    errs = []
+    for i in range(0, len(inst), max(1, len(inst) // 8)):
+        X, Q, a = inst[i]
+        idx = np.arange(0, Q.shape[0], max(1, Q.shape[0] // 16))
+        errs.append(float(np.max(oracle.rel_err(outs[i].cpu().numpy()[idx], oracle.kde(X, Q[idx], a)))))
+    recomputed = sum(k.last_recomputed() for k in kdes)
+    line = {"metric": METRIC, "value": pairs * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batched"], "instances": len(inst), "pairs_per_step": pairs,
+                       "forms": sorted({k.form for k in kdes}), "l2": "flushed between steps (512 MiB write)"},
+            "plan_s": plan_s, "datagen_s": gen_s, "gpu_launches": int(launches),
+            "recomputed_fp32_queries": int(recomputed), "max_rel_err_sampled": max(errs), "clocks": clk,
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}
+    print(json.dumps(line), flush=True)
+    for k in kdes:
+        k.close()
+    return 0
+
+
+def run_serving(args):
+    import ctypes
+    import threading
+    from paper_2407_07096_gb300 import build as B
+    from paper_2407_07096_gb300 import _lib as L
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE
+    B.build()
+    lib = L.load()
+    ns = [int(v) for v in np.round(np.exp(np.linspace(np.log(1e4), np.log(args.serve_nmax), 8)))]
+    ds_dims = [2, 4, 8, 16, 32, 64, 96, 128]
+    mixes = [G.make_mixture(50 + j, 10, d, -10.0, 10.0, 1.0) for j, d in enumerate(ds_dims)]
+    Xs = [G.sample(mixes[j], 50 + j, ns[j], "data") for j in range(8)]
+    rng = np.random.default_rng(7)
+    pool = []  # pre-generated requests: (dataset, Q)
+    for i in range(400):
+        j = int(rng.integers(0, 8))
+        m = int(np.clip(np.floor(np.exp(rng.uniform(0, np.log(4096)))), 1, 4096))
+        pool.append((j, G.sample(mixes[j], 10000 + i, m, "query")))
+    results = {}
+    for form in args.serve_forms.split(","):
+        kdes = [ExactGaussianKDE(Xs[j], 1.0 / ds_dims[j], form=form) for j in range(8)]
+        o = L.SrvOpts()
+        lib.stag_srv_opts_init(ctypes.byref(o))
+        hs = (ctypes.c_void_p * 8)(*[k._h.value for k in kdes])
+        o.datasets, o.n_datasets, o.slots, o.max_rows = hs, 8, 4, 4096
+        o.mem_budget_bytes = 8 << 30
+        srv = ctypes.c_void_p(lib.stag_srv_start(ctypes.byref(o)))
+        assert srv.value, L.last_error()
+
+        def run(rate, duration, closed=False):
+            lib.stag_srv_reset_stats(srv)
+            outs, tickets = [], []
+            lock = threading.Lock()
+            stop = threading.Event()
+
+            def waiter():
+                while not stop.is_set() or tickets:
+                    with lock:
+                        t = tickets.pop(0) if tickets else None
+                    if t is None:
+                        time.sleep(0.0005)
+                        continue
+                    lib.stag_srv_wait(srv, t, -1)
+
+            th = threading.Thread(target=waiter)
+            th.start()
+            r = np.random.default_rng(int(rate * 1000) + 1)
+            t0 = time.perf_counter()
+            next_t = t0
+            k = 0
+            pairs = 0.0
+            while time.perf_counter() - t0 < duration:
+                if not closed:
+                    next_t += r.exponential(1.0 / rate)
+                    while time.perf_counter() < next_t:
+                        time.sleep(max(0.0, min(0.001, next_t - time.perf_counter())))
+                else:
+                    while len(tickets) > 64:
+                        time.sleep(0.0002)
+                j, Q = pool[k % len(pool)]
+                k += 1
+                out = np.empty(Q.shape[0])
+                outs.append(out)
+                t = ctypes.c_uint64()
+                L.check(lib.stag_srv_submit(srv, j, Q.ctypes.data, Q.shape[0], out.ctypes.data, ctypes.byref(t)))
+                pairs += Q.shape[0] * ns[j]
+                with lock:
+                    tickets.append(t.value)
+            stop.set()
+            th.join()
+            el = time.perf_counter() - t0
+            done, rows = ctypes.c_int64(), ctypes.c_int64()
+            p50, p99 = ctypes.c_double(), ctypes.c_double()
+            lib.stag_srv_stats(srv, ctypes.byref(done), ctypes.byref(rows), ctypes.byref(p50), ctypes.byref(p99))
+            return {"offered_req_s": None if closed else rate, "achieved_req_s": done.value / el,
+                    "evals_per_s": pairs / el, "p50_ms": p50.value / 1e3, "p99_ms": p99.value / 1e3,
+                    "requests": int(done.value)}
+
+        sat = run(0, args.serve_duration, closed=True)
+        loads = {}
+        for f in (0.3, 0.6, 0.9):
+            loads[str(f)] = run(f * sat["achieved_req_s"], args.serve_duration)
+        results[form] = {"saturation": sat, "loads": loads}
+        lib.stag_srv_stop(srv)
+        for k in kdes:
+            k.close()
+    main_form = args.serve_forms.split(",")[0]
+    line = {"metric": METRIC, "value": results[main_form]["saturation"]["evals_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": None, "warmup": None, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["serving"], "n": ns, "d": ds_dims, "duration_s_per_load": args.serve_duration,
+                       "slots": 4, "max_rows": 4096},
+            "serving": results}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,11 +542,19 @@ def main():
     ap.add_argument("--m", type=int, default=None)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--serve-duration", type=float, default=8.0, help="seconds per offered load (serving)")
+    ap.add_argument("--serve-nmax", type=float, default=2e6)
+    ap.add_argument("--serve-forms", default="auto,simt_f32")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_gpu(args)
 
 

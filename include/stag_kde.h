@@ -134,6 +134,16 @@ int stag_kde_query_batch(stag_kde_t *const *hs, const void *const *dQs, const in
  */
 int stag_kde_autotune(stag_kde_t *h, const void *dQ, int64_t m);
 
+/*
+ * Degrees of the fully connected similarity graph on the handle's own points (Sec. 4.1):
+ * dOut[i] = sum_{j=1..n} exp(-a ||x_i - x_j||^2) for every point i in its original order
+ * (the density at every data point; the j = i term is exp(0) = 1). exclude_self = 1
+ * subtracts that term (1, or 1/n when normalised) afterwards, so its absolute error is that
+ * of the full sum. dOut: n doubles in device memory; asynchronous on `stream`. FP32
+ * handles only; uses the handle's query scratch.
+ */
+int stag_kde_degrees(stag_kde_t *h, int exclude_self, double *dOut, void *stream);
+
 /* Pre-sizes the handle's scratch for queries of up to m rows. */
 int stag_kde_reserve(stag_kde_t *h, int64_t m);
 

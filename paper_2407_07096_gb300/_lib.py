@@ -51,6 +51,7 @@ SIGNATURES = [
     ("stag_kde_query_batch", _INT, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_I64),
                                     ctypes.POINTER(_VP), _I64, _VP]),
     ("stag_kde_autotune", _INT, [_VP, _VP, _I64]),
+    ("stag_kde_degrees", _INT, [_VP, _INT, _VP, _VP]),
     ("stag_kde_info", _INT, [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_DBL),
                              ctypes.POINTER(_INT), ctypes.POINTER(_INT)]),
     ("stag_kde_destroy", None, [_VP]),

@@ -109,6 +109,9 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
 int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaStream_t s,
                    int *dflag);
 int ensure_partials(stag_kde *h, int64_t entries);
+// The point set in its original order, row-major (from the plain form's tiled copy).
+int simt_points_rows(stag_kde *h, float *out, cudaStream_t s);
+int launch_subtract(double *v, int64_t count, double one, cudaStream_t s);
 // Sizes the plain form's scratch (tiled queries, partials) for queries of up to m rows.
 int simt_reserve(stag_kde *h, int64_t m);
 // Recomputes with the plain FP32 form the rows idx[0 .. *count) of dQ (device count)

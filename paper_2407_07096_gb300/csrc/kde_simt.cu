@@ -98,24 +98,18 @@ __device__ __forceinline__ void merge(RowAcc &r, double oacc, float oshift) {
     r.shift = sm;
 }
 
+// One work item: query tile `qtile` (64 rows) against the point tiles of range `split`.
+// Rows at or past m_real are computed on zero padding and not stored; partials use the
+// row stride m.
 template <bool kSingleChunk>
-__global__ void __launch_bounds__(256, 2)
-kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles,
-                    const float *__restrict__ qt, int64_t m, int d_pad, float negc,
-                    int64_t tiles_per_split, double *__restrict__ part_sum,
-                    float *__restrict__ part_shift, const int *__restrict__ count) {
-    // `count` (optional, device memory): only the first *count query rows are real;
-    // blocks past them exit at once (the partials keep the row stride m)
-    const int64_t m_real = count ? (int64_t)*count : m;
-    if ((int64_t)blockIdx.x * kSimtTile >= m_real) return;
-    __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
-    __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
-
+__device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], float (*sQ)[kSimtKC * kSimtTile],
+                                          const float *__restrict__ xt, int64_t n, int64_t n_tiles,
+                                          const float *__restrict__ qt, int64_t m, int64_t m_real, int d_pad,
+                                          float negc, int64_t tiles_per_split, double *__restrict__ part_sum,
+                                          float *__restrict__ part_shift, int64_t qtile, int64_t split) {
     const int tid = threadIdx.x;
     const int tx = tid & 15;  // point group: points 4*tx .. 4*tx+3 of the tile
     const int ty = tid >> 4;  // query group: rows 4*ty .. 4*ty+3 of the block
-    const int64_t qtile = blockIdx.x;
-    const int split = blockIdx.y;
     const int64_t t0 = (int64_t)split * tiles_per_split;
     const int64_t t1 = min(n_tiles, t0 + tiles_per_split);
     const int nch = (d_pad + kSimtKC - 1) / kSimtKC;
@@ -228,6 +222,30 @@ kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles,
                 part_shift[(int64_t)split * m + q] = row[i].shift;
             }
         }
+    }
+}
+
+template <bool kSingleChunk>
+__global__ void __launch_bounds__(256, 2)
+kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, const float *__restrict__ qt, int64_t m,
+                    int d_pad, float negc, int64_t tiles_per_split, int64_t splits, double *__restrict__ part_sum,
+                    float *__restrict__ part_shift, const int *__restrict__ count) {
+    __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
+    __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
+    if (!count) {
+        // one block per (query tile, split)
+        simt_item<kSingleChunk>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum, part_shift,
+                                blockIdx.x, blockIdx.y);
+        return;
+    }
+    // `count` (device memory): only the first *count query rows are real; a fixed grid
+    // walks the (query tile, split) items those rows need
+    const int64_t rows = *count;
+    const int64_t items = ((rows + kSimtTile - 1) / kSimtTile) * splits;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+        __syncthreads();  // the previous item's shared-memory reads are done
+        simt_item<kSingleChunk>(sX, sQ, xt, n, n_tiles, qt, m, rows, d_pad, negc, tiles_per_split, part_sum,
+                                part_shift, w / splits, w % splits);
     }
 }
 
@@ -411,32 +429,37 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
     prof_start(h, s);
     if (h->d_pad <= kSimtKC)
         kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
-                                                      tps, h->part.sum, h->part.shift, nullptr);
+                                                      tps, splits, h->part.sum, h->part.shift, nullptr);
     else
         kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
-                                                       tps, h->part.sum, h->part.shift, nullptr);
+                                                       tps, splits, h->part.sum, h->part.shift, nullptr);
     prof_stop(h, s, (double)m * (double)h->n);
     STAG_CUDA_TRY(cudaGetLastError());
     return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
                           dOut, s);
 }
 
+// The recompute path serves few rows (only those the tensor-core estimate flags), so it
+// splits the point set finely and walks the work with a fixed grid.
+static int64_t fixup_splits(const stag_kde *h) { return std::max<int64_t>(1, std::min<int64_t>(h->n_tiles, 64)); }
+
 int simt_reserve(stag_kde *h, int64_t m) {
     const int64_t q_tiles = ceil_div(m, kSimtTile);
     int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
     if (rc) return rc;
     const int64_t tps = choose_tiles_per_split(h, q_tiles);
-    return ensure_partials(h, ceil_div(h->n_tiles, tps) * m);
+    const int64_t splits = std::max(ceil_div(h->n_tiles, tps), ceil_div(h->n_tiles, ceil_div(h->n_tiles, fixup_splits(h))));
+    return ensure_partials(h, splits * m);
 }
 
 int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
                     cudaStream_t s) {
     // the row set is only known on the device: size everything for all m rows and let
-    // the kernels skip what lies past *count
+    // the kernels walk only the first *count
     const int64_t q_tiles = ceil_div(m, kSimtTile);
     int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
     if (rc) return rc;
-    const int64_t tps = choose_tiles_per_split(h, q_tiles);
+    const int64_t tps = ceil_div(h->n_tiles, fixup_splits(h));
     const int64_t splits = ceil_div(h->n_tiles, tps);
     rc = ensure_partials(h, splits * m);
     if (rc) return rc;
@@ -444,15 +467,43 @@ int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, con
     gather_rows_tiles_kernel<<<grid_for(q_tiles * h->d_pad * kSimtTile, 256), 256, 0, s>>>(dQ, h->d, h->d_pad, idx,
                                                                                            count, m, h->qt);
     const float negc = (float)(-h->a * 1.4426950408889634);
-    dim3 grid((unsigned)q_tiles, (unsigned)splits);
+    const unsigned grid = (unsigned)(h->sm_count * 2);
     if (h->d_pad <= kSimtKC)
-        kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
+        kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps, splits,
                                                       h->part.sum, h->part.shift, count);
     else
         kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
-                                                       h->part.sum, h->part.shift, count);
+                                                       splits, h->part.sum, h->part.shift, count);
     combine_scatter_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
         h->part.sum, h->part.shift, m, (int)splits, idx, count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+// Tile-transposed [tile][d_pad][64] back to row-major n x d.
+__global__ void tiles_to_rows_kernel(const float *__restrict__ xt, int64_t n, int64_t d, int d_pad,
+                                     float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * d; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = i / d, k = i % d;
+        out[i] = xt[((row / kSimtTile) * d_pad + k) * kSimtTile + row % kSimtTile];
+    }
+}
+
+__global__ void subtract_one_kernel(double *__restrict__ v, int64_t count, double one) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] -= one;
+}
+
+int simt_points_rows(stag_kde *h, float *out, cudaStream_t s) {
+    count_launch();
+    tiles_to_rows_kernel<<<grid_for(h->n * h->d, 256), 256, 0, s>>>(h->xt, h->n, h->d, h->d_pad, out);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int launch_subtract(double *v, int64_t count, double one, cudaStream_t s) {
+    count_launch();
+    subtract_one_kernel<<<grid_for(count, 256), 256, 0, s>>>(v, count, one);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }

@@ -811,56 +811,63 @@ __global__ void tc_split_queries_kernel(const float *__restrict__ Q, int64_t m, 
     }
 }
 
-// R[t][q] = c * ||q - c_t||^2 by direct differences in FP32 (padding queries: 0).
-// One block per (128-query tile, group of point tiles); queries staged transposed.
+// R[t][q] = c * ||q - c_t||^2 by direct differences in FP32 (padding queries: 0), the
+// per-query upper bound on every exponent, and ||q - c_g||.
+// One thread per query (its coordinates in registers), 128 queries per block, the tile
+// centres of a group of 32 tiles staged in shared memory and read as broadcasts.
+template <int KP>
 __global__ void __launch_bounds__(128)
-tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
-                  const float *__restrict__ cent, int64_t T, int tiles_per_block, float c, float *__restrict__ R,
-                  const float *__restrict__ cg, float *__restrict__ unorm, const float *__restrict__ tinfo,
-                  unsigned *__restrict__ ub) {
-    extern __shared__ float sq[];  // [Kp][128]
+tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_pad, const float *__restrict__ cent,
+                  int64_t T, int tiles_per_block, float c, float *__restrict__ R, const float *__restrict__ cg,
+                  float *__restrict__ unorm, const float *__restrict__ tinfo, unsigned *__restrict__ ub) {
+    constexpr int TG = 32;  // tiles per shared-memory group
+    __shared__ __align__(16) float sc[TG][KP];
+    __shared__ float srad[TG];
     const int64_t q0 = (int64_t)blockIdx.x * 128;
     const int r = threadIdx.x;
-    for (int k = 0; k < Kp; ++k) {
-        const int64_t q = q0 + r;
-        sq[k * 128 + r] = (q < m && k < d) ? Q[q * d + k] : 0.f;
-    }
-    __syncthreads();
+    const bool real = q0 + r < m;
+    float qv[KP];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) qv[k] = (real && k < d) ? Q[(q0 + r) * d + k] : 0.f;
     if (blockIdx.y == 0) {
         float s = 0.f;
-        for (int k = 0; k < Kp; ++k) {
-            const float df = sq[k * 128 + r] - cg[k];
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const float df = qv[k] - cg[k];
             s = fmaf(df, df, s);
         }
-        unorm[q0 + r] = q0 + r < m ? sqrtf(s) : 0.f;
+        unorm[q0 + r] = real ? sqrtf(s) : 0.f;
     }
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
-    const bool real = q0 + r < m;
     // upper bound on the exponent -c ||q - x||^2 over the tiles of this block: every x of
     // tile t lies within the tile's max radius rho_t of c_t, so
     //     -c ||q - x||^2 <= -( max(0, sqrt(c R') - sqrt(c) rho_t) )^2,  R' = ||q - c_t||^2
     const float sqc = sqrtf(c);
     float ubest = -INFINITY;
-    for (int64_t t = ta; t < tb; ++t) {
-        const float4 *ct = reinterpret_cast<const float4 *>(cent + t * Kp);
-        float s0 = 0.f, s1 = 0.f;
-        for (int k4 = 0; k4 < Kp / 4; ++k4) {
-            const float4 cv = __ldg(ct + k4);
-            const float d0 = sq[(4 * k4 + 0) * 128 + r] - cv.x;
-            const float d1 = sq[(4 * k4 + 1) * 128 + r] - cv.y;
-            const float d2 = sq[(4 * k4 + 2) * 128 + r] - cv.z;
-            const float d3 = sq[(4 * k4 + 3) * 128 + r] - cv.w;
-            s0 = fmaf(d0, d0, s0);
-            s1 = fmaf(d1, d1, s1);
-            s0 = fmaf(d2, d2, s0);
-            s1 = fmaf(d3, d3, s1);
+    for (int64_t g0 = ta; g0 < tb; g0 += TG) {
+        const int gn = (int)min((int64_t)TG, tb - g0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < gn * KP; e += 128) sc[e / KP][e % KP] = cent[(g0 + e / KP) * KP + e % KP];
+        for (int e = threadIdx.x; e < gn; e += 128) srad[e] = tinfo[(g0 + e) * 4 + 1];
+        __syncthreads();
+        for (int j = 0; j < gn; ++j) {
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < KP; k += 4) {
+                const float4 cv = *reinterpret_cast<const float4 *>(&sc[j][k]);
+                const float d0 = qv[k] - cv.x, d1 = qv[k + 1] - cv.y, d2 = qv[k + 2] - cv.z, d3 = qv[k + 3] - cv.w;
+                s0 = fmaf(d0, d0, s0);
+                s1 = fmaf(d1, d1, s1);
+                s0 = fmaf(d2, d2, s0);
+                s1 = fmaf(d3, d3, s1);
+            }
+            const float cr = c * (s0 + s1);
+            R[(g0 + j) * m_pad + q0 + r] = real ? cr : 0.f;
+            // slack of a few ulps so that the bound holds for the FP32-computed exponents too
+            const float gap = fmaxf(0.f, sqrtf(cr) * (1.f - 1e-5f) - sqc * srad[j]);
+            ubest = fmaxf(ubest, -gap * gap);
         }
-        const float cr = c * (s0 + s1);
-        R[t * m_pad + q0 + r] = real ? cr : 0.f;
-        // slack of a few ulps so that the bound holds for the FP32-computed exponents too
-        const float gap = fmaxf(0.f, sqrtf(cr) * (1.f - 1e-5f) - sqc * __ldg(tinfo + t * 4 + 1));
-        ubest = fmaxf(ubest, -gap * gap);
     }
     if (tb > ta) atomicMax(ub + q0 + r, float_order_bits(real ? ubest : 0.f));
 }
@@ -1192,14 +1199,19 @@ static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     tc_split_queries_kernel<<<grid_for(m_pad * Kp, 256), 256, 0, s>>>(dQ, m, h->d, Kp, m_pad, tc->cg, tc->scales,
                                                                       tc->a_hi, tc->a_lo, tc->qbad);
     const int tpb = 64;
-    static std::once_flag attr_once;
-    std::call_once(attr_once, []() {
-        cudaFuncSetAttribute(tc_rowterm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 128 * 4);
-    });
     dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
-    tc_rowterm_kernel<<<grid, 128, Kp * 128 * sizeof(float), s>>>(dQ, m, h->d, Kp, m_pad, tc->cent, tc->T, tpb,
-                                                                  (float)c, tc->rowterm, tc->cg, tc->unorm, tc->tinfo,
-                                                                  tc->ub);
+    switch (Kp) {
+#define STAG_ROWTERM(KPV)                                                                                          \
+    case KPV:                                                                                                      \
+        tc_rowterm_kernel<KPV><<<grid, 128, 0, s>>>(dQ, m, h->d, m_pad, tc->cent, tc->T, tpb, (float)c, tc->rowterm, \
+                                                    tc->cg, tc->unorm, tc->tinfo, tc->ub);                         \
+        break;
+        STAG_ROWTERM(16)
+        STAG_ROWTERM(32)
+        STAG_ROWTERM(64)
+        STAG_ROWTERM(128)
+#undef STAG_ROWTERM
+    }
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }

@@ -368,6 +368,23 @@ int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, v
     return run_query(h, dQ, m, dOut, (cudaStream_t)stream, nullptr);
 }
 
+int stag_kde_degrees(stag_kde_t *h, int exclude_self, double *dOut, void *stream) {
+    if (!h || !dOut) return fail(STAG_KDE_EINVAL, "handle or dOut is NULL");
+    if (h->dtype != STAG_KDE_F32) return fail(STAG_KDE_EUNSUPPORTED, "degrees: FP32 handles only");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    // the point set in original order, as a query batch against itself
+    int rc = ensure_bytes(&h->q_dev, &h->q_dev_cap, h->n * h->d * (int64_t)sizeof(float));
+    if (rc) return rc;
+    rc = simt_points_rows(h, (float *)h->q_dev, s);
+    if (rc) return rc;
+    rc = run_query(h, h->q_dev, h->n, dOut, s, nullptr);
+    if (rc) return rc;
+    if (exclude_self) rc = launch_subtract(dOut, h->n, h->normalise ? 1.0 / (double)h->n : 1.0, s);
+    return rc;
+}
+
 int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *dtype, int *form) {
     if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
     if (n) *n = h->n;

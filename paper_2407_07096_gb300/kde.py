@@ -106,6 +106,15 @@ class ExactGaussianKDE:
         L.check(self._lib.stag_kde_profile_end(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)))
         return ms.value, n.value, pairs.value
 
+    def degrees(self, exclude_self: bool = False, stream=None):
+        """Similarity-graph degrees of the handle's own points (Sec. 4.1), a CUDA tensor."""
+        import torch
+        out = torch.empty(self.n, dtype=torch.float64, device="cuda")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        L.check(self._lib.stag_kde_degrees(self._h, 1 if exclude_self else 0, out.data_ptr(),
+                                           ctypes.c_void_p(s.cuda_stream)))
+        return out
+
     def autotune(self, Q):
         """Tunes the tensor-core launch settings on the CUDA query tensor Q."""
         L.check(self._lib.stag_kde_autotune(self._h, Q.data_ptr(), Q.shape[0]))
