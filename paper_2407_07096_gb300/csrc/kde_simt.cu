@@ -23,6 +23,7 @@
 // bitwise reproducible.
 #include <math.h>
 
+#include "f32x2.cuh"
 #include "internal.h"
 
 namespace stagkde {
@@ -139,11 +140,10 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
     if (iters > 0) load(0, t0, 0);
     cp_async_commit();
 
-    float d2[4][4];
+    // squared distances of the 4 x 4 pairs, as packed column pairs (4*tx+0,1) and (+2,3)
+    uint64_t d2p[4][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) d2[i][j] = 0.f;
+    for (int i = 0; i < 4; ++i) d2p[i][0] = d2p[i][1] = 0ull;
 
     int group = 0;
     for (int64_t it = 0; it < iters; ++it) {
@@ -166,14 +166,14 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
             const float4 qv = *reinterpret_cast<const float4 *>(&qs[k * kSimtTile + ty * 4]);
             const float4 xv = *reinterpret_cast<const float4 *>(&xs[k * kSimtTile + tx * 4]);
             const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-            const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+            const uint64_t x01 = f2::pack(xv.x, xv.y), x23 = f2::pack(xv.z, xv.w);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float df = qa[i] - xa[j];
-                    d2[i][j] = fmaf(df, df, d2[i][j]);
-                }
+            for (int i = 0; i < 4; ++i) {
+                const uint64_t qq = f2::pack(qa[i], qa[i]);
+                const uint64_t df0 = f2::sub(qq, x01), df1 = f2::sub(qq, x23);
+                d2p[i][0] = f2::fma(df0, df0, d2p[i][0]);
+                d2p[i][1] = f2::fma(df1, df1, d2p[i][1]);
+            }
         }
         __syncthreads();
 
@@ -182,11 +182,13 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
             const int64_t col0 = t * kSimtTile + tx * 4;
             const int valid = (int)max((int64_t)0, min((int64_t)4, n - col0));
 #pragma unroll
-            for (int i = 0; i < 4; ++i) add_terms(row[i], d2[i], negc, valid);
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) d2[i][j] = 0.f;
+            for (int i = 0; i < 4; ++i) {
+                float d2[4];
+                f2::unpack(d2p[i][0], d2[0], d2[1]);
+                f2::unpack(d2p[i][1], d2[2], d2[3]);
+                add_terms(row[i], d2, negc, valid);
+                d2p[i][0] = d2p[i][1] = 0ull;
+            }
             if (++group == kFlushTiles) {
                 group = 0;
 #pragma unroll
