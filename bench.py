@@ -187,6 +187,23 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def recorded_traffic(workload, form):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu capture, if the
+    kernel's source is unchanged since (same SHA-256); otherwise None."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(workload)
+        if not rec or form != "tc":
+            return None
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
+                return None
+        return rec["dram_bytes_per_launch"]
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 # Per-SM-per-clock unit counts used for the ALU-bound rooflines (see DESIGN.md):
 FP32_LANES_PER_SM = 128       # FFMA lanes per SM per clock
 EX2_PER_SM_CLK = 32.0         # MUFU ex2 results per SM per clock (measured by the probe)
@@ -338,7 +355,9 @@ def run_gpu(args):
            "steps": e2e_steps}
 
     peaks, peak_kind = load_peaks()
+    traffic = recorded_traffic(args.workload, form)
     roof = roofline_for(form, d, kern_pairs / max(kern_launches, 1), kern_ms / max(kern_launches, 1), clk, peaks)
+    roof["traffic"] = traffic
     roof["peak_source"] = peak_kind if roof["bound"] == "tensor" else "derived from unit counts x sampled SM clock"
     roof["kernel_ms_per_launch"] = kern_ms / max(kern_launches, 1)
 
