@@ -44,6 +44,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <mutex>
 
 #include "internal.h"
@@ -209,16 +210,14 @@ __device__ __forceinline__ float order_bits_to_float(uint32_t o) {
     return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
 }
 
-// A row's running sums in units of 2^shift. The tile's sum (acc32) is folded into a
-// compensated FP32 sum (ksum, kc; Kahan) after every tile, which keeps ~2^-24 relative
-// accuracy over thousands of tiles without touching the slow FP64 pipe in the loop;
-// FP64 is used once per work unit.
+// A row's running sums in units of 2^shift. Each tile's sum is folded into a compensated
+// FP32 sum (ksum, kc; Kahan), which keeps ~2^-24 relative accuracy over thousands of
+// tiles without touching the slow FP64 pipe in the loop; FP64 is used once per work unit.
 struct RowState {
     float shift;
-    float acc32;  // current tile
-    float ksum;   // compensated sum of the tiles so far
-    float kc;     // its compensation term
-    float w32;    // sum over chunks of (chunk sum) * (tile RMS radius), same units as acc
+    float ksum;  // compensated sum of the tiles so far
+    float kc;    // its compensation term
+    float w32;   // sum over tiles of (tile sum) * (tile RMS radius), same units as ksum
 };
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
@@ -228,41 +227,31 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
-// Sum of 2^(kk*D[j] + nb) over the first `valid` of 32 columns (valid = 32 except in the
-// point set's last, padded tile); nb = -(c R + s) with the row's fixed shift s, which
-// bounds every exponent from above, so no term exceeds ~1 and no rescaling is needed.
-// Two independent packed accumulators keep the dependency chains short.
-__device__ __forceinline__ void epi_chunk(RowState &st, const uint32_t (&D)[32], float kk, float nb, float vrad,
-                                          int valid) {
-    float cs;
-    if (valid == 32) {
-        const uint64_t kk2 = pack2(kk, kk);
-        const uint64_t nb2 = pack2(nb, nb);
-        uint64_t acc_a = 0, acc_b = 0;  // {0.f, 0.f}
+// Adds 2^(kk*D[j] + nb) for the 32 columns of one TMEM chunk into two packed accumulators
+// (four independent FP32 chains). nb = -(c R + s) with the row's fixed shift s, which bounds
+// every exponent from above, so no term exceeds ~1 and no rescaling is needed. kMasked:
+// only the first `valid` columns hold real points (the point set's last, padded tile).
+template <bool kMasked>
+__device__ __forceinline__ void epi_chunk(uint64_t &acc_a, uint64_t &acc_b, const uint32_t (&D)[32], uint64_t kk2,
+                                          uint64_t nb2, int valid) {
 #pragma unroll
-        for (int j = 0; j < 32; j += 4) {
-            const uint64_t x01 = fma2(kk2, pack2(__uint_as_float(D[j]), __uint_as_float(D[j + 1])), nb2);
-            const uint64_t x23 = fma2(kk2, pack2(__uint_as_float(D[j + 2]), __uint_as_float(D[j + 3])), nb2);
-            float a0, a1, a2, a3;
-            unpack2(x01, a0, a1);
-            unpack2(x23, a2, a3);
-            acc_a = add2(acc_a, pack2(ptx::ex2_approx(a0), ptx::ex2_approx(a1)));
-            acc_b = add2(acc_b, pack2(ptx::ex2_approx(a2), ptx::ex2_approx(a3)));
+    for (int j = 0; j < 32; j += 4) {
+        const uint64_t x01 = fma2(kk2, pack2(__uint_as_float(D[j]), __uint_as_float(D[j + 1])), nb2);
+        const uint64_t x23 = fma2(kk2, pack2(__uint_as_float(D[j + 2]), __uint_as_float(D[j + 3])), nb2);
+        float a0, a1, a2, a3;
+        unpack2(x01, a0, a1);
+        unpack2(x23, a2, a3);
+        float e0 = ptx::ex2_approx(a0), e1 = ptx::ex2_approx(a1);
+        float e2 = ptx::ex2_approx(a2), e3 = ptx::ex2_approx(a3);
+        if constexpr (kMasked) {
+            e0 = j < valid ? e0 : 0.f;
+            e1 = j + 1 < valid ? e1 : 0.f;
+            e2 = j + 2 < valid ? e2 : 0.f;
+            e3 = j + 3 < valid ? e3 : 0.f;
         }
-        float s0, s1, s2, s3;
-        unpack2(acc_a, s0, s1);
-        unpack2(acc_b, s2, s3);
-        cs = (s0 + s1) + (s2 + s3);
-    } else {
-        cs = 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float e = ptx::ex2_approx(fmaf(kk, __uint_as_float(D[j]), nb));
-            cs += j < valid ? e : 0.f;
-        }
+        acc_a = add2(acc_a, pack2(e0, e1));
+        acc_b = add2(acc_b, pack2(e2, e3));
     }
-    st.acc32 += cs;
-    st.w32 = fmaf(cs, vrad, st.w32);
 }
 
 template <int KP, int BN, int SB, int SMETA, int AB, int EG>
@@ -493,92 +482,108 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
         float *mshift = reinterpret_cast<float *>(mw + (EG - 1) * BM);     // [EG-1][BM]
         uint32_t tcount = 0, ucount = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
-            const TcInst &I = *find_inst(insts, n_inst, u);
-            const int64_t lu = u - I.unit_begin;
-            const int64_t split = lu / I.q_tiles, qt = lu % I.q_tiles;
-            const int64_t t0 = split * I.tiles_per_split;
-            const int64_t t1 = min(I.T, t0 + I.tiles_per_split);
-            const float kk = I.scales[2];
-            // the row's fixed shift: ceil of an upper bound on every exponent of the row
-            const float s_row = ceilf(order_bits_to_float(I.ub[qt * BM + row]));
-            RowState st{s_row, 0.f, 0.f, 0.f, 0.f};
-            for (int64_t t = t0; t < t1; ++t, ++tcount) {
-                const int acc = tcount & 1;
-                const int ms = tcount % SMETA;
-                // lane 0 waits (the other lanes do not spend issue slots polling); the
-                // outcome is broadcast so that the warp never splits around __syncwarp
-                bool got = true;
-                if (lane == 0)
-                    got = ptx::mbar_wait_bounded(&acc_full[acc], (tcount >> 1) & 1, kWaitLimitNs, abort_flag) &&
-                          ptx::mbar_wait_bounded(&full_m[ms], (tcount / SMETA) & 1, kWaitLimitNs, abort_flag);
-                if (!__shfl_sync(0xffffffffu, (int)got, 0)) {
-                    timed_out();
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-                const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
-                const float nb = -(meta[row] + st.shift);
-                const float vrad = meta[BM];
-                // real points among this warp's columns (only the last tile is padded)
-                int vcols = COLS;
-                if (t == I.T - 1) vcols = (int)max((int64_t)0, min((int64_t)COLS, I.n - (t * BN + grp * COLS)));
-                const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS;
-                if constexpr (EG >= 4 || NCH == 1) {
-                    // enough warps per scheduler to hide the TMEM load latency: one buffer
+        RowState st{0.f, 0.f, 0.f, 0.f};
+        // One tile of this warp's columns: wait for its accumulator and row terms, sum
+        // the exponentials, release both, fold the sum into the row state. Returns false
+        // on timeout or abort.
+        auto tile = [&](auto masked, uint64_t kk2, int vcols) -> bool {
+            constexpr bool kMasked = decltype(masked)::value;
+            const int acc = tcount & 1;
+            const int ms = tcount % SMETA;
+            // lane 0 waits (the other lanes do not spend issue slots polling); the outcome
+            // is broadcast so that the warp never splits around __syncwarp
+            bool got = true;
+            if (lane == 0)
+                got = ptx::mbar_wait_bounded(&acc_full[acc], (tcount >> 1) & 1, kWaitLimitNs, abort_flag) &&
+                      ptx::mbar_wait_bounded(&full_m[ms], (tcount / SMETA) & 1, kWaitLimitNs, abort_flag);
+            if (!__shfl_sync(0xffffffffu, (int)got, 0)) return false;
+            ptx::tc_fence_after();
+            const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
+            const float nb = -(meta[row] + st.shift);
+            const float vrad = meta[BM];
+            const uint64_t nb2 = pack2(nb, nb);
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS;
+            uint64_t acc_a = 0, acc_b = 0;  // {0.f, 0.f}
+            auto release_acc = [&]() {
+                // every TMEM column of this buffer has been read: hand it back to the MMA
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
+            };
+            if constexpr (EG >= 4 || NCH == 1) {
+                // enough warps per scheduler to hide the TMEM load latency: one buffer
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        uint32_t Da[32];
-                        ptx::tmem_ld_32x32b_x32(taddr + c * 32, Da);
-                        ptx::tmem_ld_wait();
-                        ptx::reg_fence32(Da);
-                        if (c + 1 == NCH) {
-                            ptx::tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
-                        }
-                        epi_chunk(st, Da, kk, nb, vrad, min(32, max(0, vcols - c * 32)));
-                    }
-                } else {
-                    // software pipeline: the TMEM load of chunk c+1 is in flight while chunk
-                    // c is processed (tcgen05.wait::ld waits for every load issued before it)
-                    uint32_t Da[32], Db[32];
-                    ptx::tmem_ld_32x32b_x32(taddr, Da);
+                for (int c = 0; c < NCH; ++c) {
+                    uint32_t Da[32];
+                    ptx::tmem_ld_32x32b_x32(taddr + c * 32, Da);
                     ptx::tmem_ld_wait();
                     ptx::reg_fence32(Da);
+                    if (c + 1 == NCH) release_acc();
+                    epi_chunk<kMasked>(acc_a, acc_b, Da, kk2, nb2, vcols - c * 32);
+                }
+            } else {
+                // software pipeline: the TMEM load of chunk c+1 is in flight while chunk c
+                // is processed (tcgen05.wait::ld waits for every load issued before it)
+                uint32_t Da[32], Db[32];
+                ptx::tmem_ld_32x32b_x32(taddr, Da);
+                ptx::tmem_ld_wait();
+                ptx::reg_fence32(Da);
 #pragma unroll
-                    for (int c = 0; c < NCH; ++c) {
-                        if (c + 1 < NCH) {
-                            if (c & 1)
-                                ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Da);
-                            else
-                                ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Db);
-                        } else {
-                            // every TMEM column of this buffer has been read: hand it back
-                            ptx::tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
-                        }
+                for (int c = 0; c < NCH; ++c) {
+                    if (c + 1 < NCH) {
                         if (c & 1)
-                            epi_chunk(st, Db, kk, nb, vrad, min(32, max(0, vcols - c * 32)));
+                            ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Da);
                         else
-                            epi_chunk(st, Da, kk, nb, vrad, min(32, max(0, vcols - c * 32)));
-                        if (c + 1 < NCH) {
-                            ptx::tmem_ld_wait();
-                            if (c & 1)
-                                ptx::reg_fence32(Da);
-                            else
-                                ptx::reg_fence32(Db);
-                        }
+                            ptx::tmem_ld_32x32b_x32(taddr + (c + 1) * 32, Db);
+                    } else {
+                        release_acc();
+                    }
+                    if (c & 1)
+                        epi_chunk<kMasked>(acc_a, acc_b, Db, kk2, nb2, vcols - c * 32);
+                    else
+                        epi_chunk<kMasked>(acc_a, acc_b, Da, kk2, nb2, vcols - c * 32);
+                    if (c + 1 < NCH) {
+                        ptx::tmem_ld_wait();
+                        if (c & 1)
+                            ptx::reg_fence32(Da);
+                        else
+                            ptx::reg_fence32(Db);
                     }
                 }
-                __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&empty_m[ms]);
-                kahan_add(st.ksum, st.kc, st.acc32);
-                st.acc32 = 0.f;
             }
-            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty_m[ms]);
+            float s0, s1, s2, s3;
+            unpack2(acc_a, s0, s1);
+            unpack2(acc_b, s2, s3);
+            const float ts = (s0 + s1) + (s2 + s3);
+            kahan_add(st.ksum, st.kc, ts);
+            st.w32 = fmaf(ts, vrad, st.w32);
+            ++tcount;
+            return true;
+        };
+        for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+            // everything the tile loop needs is read once per unit, into registers
+            const TcInst &I = *find_inst(insts, n_inst, u);
+            const int64_t lu = u - I.unit_begin;
+            const int64_t q_tiles = I.q_tiles, T = I.T;
+            const int64_t split = lu / q_tiles, qt = lu - split * q_tiles;
+            const int64_t t0 = split * I.tiles_per_split;
+            const int64_t t1 = min(T, t0 + I.tiles_per_split);
+            const float kk = I.scales[2];
+            const uint64_t kk2 = pack2(kk, kk);
+            // real points among this warp's columns of the point set's last tile
+            const int vlast = (int)max((int64_t)0, min((int64_t)COLS, I.n - (T - 1) * BN - grp * COLS));
+            const bool masked_end = t1 == T && vlast < COLS;
+            const int n_full = (int)(t1 - t0) - (masked_end ? 1 : 0);
+            // the row's fixed shift: ceil of an upper bound on every exponent of the row
+            st = RowState{ceilf(order_bits_to_float(I.ub[qt * BM + row])), 0.f, 0.f, 0.f};
+            for (int i = 0; i < n_full && ok; ++i) ok = tile(std::false_type{}, kk2, COLS);
+            if (ok && masked_end) ok = tile(std::true_type{}, kk2, vlast);
+            if (!ok) {
+                timed_out();
+                break;
+            }
             const double acc64 = (double)st.ksum - (double)st.kc;
             const double w64 = (double)st.w32;
             // merge the column groups of each row (groups 1.. hand their sums to group 0
