@@ -26,10 +26,16 @@
 //               constant column), per point tile the B planes (v_hi, v_lo, -g pieces)
 //               and a metadata block (R of the unit's 128 queries, the tile's RMS
 //               radius) into rings of stages;
-//   warp 1      allocates TMEM; one thread issues 3 * K/16 + 1 MMAs per tile into one of
-//               two TMEM accumulators (128 lanes x BN columns, FP32) and commits;
-//   4*EG warps  epilogue: each thread owns one query row (its TMEM lane) and BN/EG of
-//               the tile's columns: tcgen05.ld, packed FMA, ex2, packed add.
+//   warp 1      allocates TMEM; one thread issues 3 * K/16 + 1 MMAs per accumulator
+//               and commits. K = 16 ("ring"): four accumulators of 128 lanes x BN/2
+//               FP32 columns, half tile k into accumulator k mod 4; K >= 32: two
+//               accumulators of BN columns, tile t into accumulator t mod 2;
+//   4*EG warps  epilogue, EG groups of 4 warps (one per TMEM lane quadrant), each
+//               thread one query row (its TMEM lane): tcgen05.ld, packed FMA, ex2,
+//               packed add. Ring: group g takes the half tiles k with k mod EG = g and
+//               waits only for its own accumulators, so the groups drift apart by up to
+//               a tile without stalling one another; K >= 32: group g takes BN/EG
+//               columns of every tile, so an accumulator is drained by all warps at once.
 // A work unit is (query tile of 128 rows, contiguous range of point tiles); the partial
 // sums per (range, query) are combined in FP64, together with a per-query error
 // estimate, by tc_combine_kernel; queries whose estimate is too large are recomputed by
@@ -142,12 +148,25 @@ struct Cfg {
     static constexpr int OFF_META = OFF_B + SB * B_BYTES;
     static constexpr int OFF_MERGE = OFF_META + SMETA * META_STRIDE;
     static constexpr int OFF_BAR = OFF_MERGE + BM * 24 * (EG - 1);
-    static constexpr int NBAR = 2 * SB + 2 * SMETA + 2 * AB + 4 + 3;
+    static constexpr int NBAR = 2 * SB + 2 * SMETA + 2 * AB + 2 * 4 + 3;  // 4: accumulators, at most
     static constexpr int OFF_MISC = OFF_BAR + NBAR * 8;
     static constexpr int BYTES = OFF_MISC + 64;
     static constexpr int SMEM = BYTES + 1024;  // + alignment slack
-    static constexpr uint32_t TMEM_COLS = 2 * BN;
-    static constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, BN);
+    // Accumulator layout. RING (K = 16, where the epilogue's ex2 rate is the bound): four
+    // TMEM accumulators of BN/2 columns, one per half tile, each owned by one epilogue
+    // group, so the groups run up to a tile apart without waiting for one another.
+    // Otherwise (K >= 32, where the tensor pipe has less slack and the N = BN MMAs are
+    // more efficient): two accumulators of BN columns shared by all groups, each group
+    // taking BN/EG columns of every tile, which hands an accumulator back sooner.
+    static constexpr bool RING = KP <= 16;
+    static constexpr int NACC = RING ? 4 : 2;
+    static constexpr int ACC_COLS = RING ? BN / 2 : BN;
+    static constexpr int WCOLS = RING ? BN / 2 : BN / EG;     // columns one warp reads per visit
+    static constexpr int ACC_READERS = RING ? 4 : 4 * EG;     // warps reading one accumulator
+    static constexpr int META_READERS = RING ? 8 : 4 * EG;    // warps reading one tile's row terms
+    static constexpr uint32_t TMEM_COLS = NACC * ACC_COLS;
+    static constexpr uint32_t IDESC = ptx::idesc_f16_f32(BM, ACC_COLS);
+    static_assert(!RING || NACC % EG == 0, "every accumulator belongs to one epilogue group");
     static_assert(A_PLANE % 1024 == 0 && B_PLANE % 1024 == 0 && A_AUG % 1024 == 0 && B_AUG % 1024 == 0,
                   "planes must keep 1024-byte alignment");
 };
@@ -156,7 +175,7 @@ struct Cfg {
 // instances of the same operand width; the units of instance i are the global unit
 // indices [unit_begin, unit_begin + q_tiles * splits). The tensor maps sit in this
 // struct, in kernel-parameter space (one instance) or global memory (a batch table).
-struct alignas(64) TcInst {
+struct TcInst {
     CUtensorMap map_ahi, map_alo, map_aaug, map_bhi, map_blo, map_baug;
     const float *tinfo;    // [T][4]
     const float *rowterm;  // [T][m_pad]
@@ -271,8 +290,8 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
     uint64_t *a_full = empty_m + SMETA;
     uint64_t *a_empty = a_full + AB;
     uint64_t *acc_full = a_empty + AB;
-    uint64_t *acc_empty = acc_full + 2;
-    uint64_t *merge_full = acc_empty + 2;
+    uint64_t *acc_empty = acc_full + 4;
+    uint64_t *merge_full = acc_empty + 4;
     uint64_t *merge_empty = merge_full + 1;
     uint64_t *drain = merge_empty + 1;
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + C::OFF_MISC);
@@ -288,15 +307,15 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
         }
         for (int i = 0; i < SMETA; ++i) {
             ptx::mbar_init(&full_m[i], 1);
-            ptx::mbar_init(&empty_m[i], 4 * EG);
+            ptx::mbar_init(&empty_m[i], C::META_READERS);
         }
         for (int i = 0; i < AB; ++i) {
             ptx::mbar_init(&a_full[i], 1);
             ptx::mbar_init(&a_empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < C::NACC; ++i) {
             ptx::mbar_init(&acc_full[i], 1);
-            ptx::mbar_init(&acc_empty[i], 4 * EG);
+            ptx::mbar_init(&acc_empty[i], C::ACC_READERS);
         }
         ptx::mbar_init(merge_full, 4 * (EG - 1));
         ptx::mbar_init(merge_empty, 4);
@@ -422,13 +441,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 }
                 ptx::tc_fence_after();
                 const uint32_t abase = a0 + ab * C::A_BYTES;
-                for (int64_t t = t0; t < t1; ++t, ++tcount) {
-                    const int acc = tcount & 1;
-                    if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((tcount >> 1) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
-                        timed_out();
-                        ok = false;
-                        break;
-                    }
+                for (int64_t t = t0; t < t1 && ok; ++t, ++tcount) {
                     const int sb = tcount % SB;
                     if (!ptx::mbar_wait_bounded(&full_b[sb], (tcount / SB) & 1, kWaitLimitNs, abort_flag)) {
                         timed_out();
@@ -437,29 +450,57 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                     }
                     ptx::tc_fence_after();
                     const uint32_t bbase = b0 + sb * C::B_BYTES;
-                    const uint32_t d_tmem = tmem_base + acc * BN;
-                    uint32_t accumulate = 0;
+                    // 3 * K/16 + 1 MMAs: the split products, then the point term
+                    auto issue = [&](uint32_t d_tmem, uint32_t idesc, uint32_t row0) {
+                        uint32_t accumulate = 0;
 #pragma unroll
-                    for (int prod = 0; prod < 3; ++prod) {
-                        // (u_hi, v_hi), (u_hi, v_lo), (u_lo, v_hi)
-                        const uint32_t ap = abase + (prod == 2 ? C::A_PLANE : 0);
-                        const uint32_t bp = bbase + (prod == 1 ? C::B_PLANE : 0);
+                        for (int prod = 0; prod < 3; ++prod) {
+                            // (u_hi, v_hi), (u_hi, v_lo), (u_lo, v_hi); B rows row0..
+                            const uint32_t ap = abase + (prod == 2 ? C::A_PLANE : 0);
+                            const uint32_t bp = bbase + (prod == 1 ? C::B_PLANE : 0) + row0 * G::CW * 2;
 #pragma unroll
-                        for (int s = 0; s < KP / 16; ++s) {
-                            const uint64_t ad = ptx::smem_desc(ap + G::koff(s, BM), 16, G::SBO, G::SW);
-                            const uint64_t bd = ptx::smem_desc(bp + G::koff(s, BN), 16, G::SBO, G::SW);
-                            ptx::mma_f16(d_tmem, ad, bd, C::IDESC, accumulate);
-                            accumulate = 1;
+                            for (int s = 0; s < KP / 16; ++s) {
+                                const uint64_t ad = ptx::smem_desc(ap + G::koff(s, BM), 16, G::SBO, G::SW);
+                                const uint64_t bd = ptx::smem_desc(bp + G::koff(s, BN), 16, G::SBO, G::SW);
+                                ptx::mma_f16(d_tmem, ad, bd, idesc, accumulate);
+                                accumulate = 1;
+                            }
                         }
-                    }
-                    {
-                        // the point term: constant A column x (-g/2) pieces, one K = 16 step
+                        // constant A column x (-g/2) pieces, one K = 16 step
                         const uint64_t ad = ptx::smem_desc(abase + 2 * C::A_PLANE, 16, 256, ptx::kSw32);
-                        const uint64_t bd = ptx::smem_desc(bbase + 2 * C::B_PLANE, 16, 256, ptx::kSw32);
-                        ptx::mma_f16(d_tmem, ad, bd, C::IDESC, 1);
+                        const uint64_t bd = ptx::smem_desc(bbase + 2 * C::B_PLANE + row0 * 32, 16, 256, ptx::kSw32);
+                        ptx::mma_f16(d_tmem, ad, bd, idesc, 1);
+                    };
+                    if constexpr (C::RING) {
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t k = 2 * tcount + h;  // half tile index, CTA-wide
+                            const int acc = k % C::NACC;
+                            if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((k / C::NACC) & 1) ^ 1, kWaitLimitNs,
+                                                        abort_flag)) {
+                                timed_out();
+                                ok = false;
+                                break;
+                            }
+                            ptx::tc_fence_after();
+                            issue(tmem_base + acc * C::ACC_COLS, C::IDESC, h * C::ACC_COLS);
+                            ptx::mma_commit(&acc_full[acc]);
+                        }
+                    } else {
+                        const int acc = tcount % C::NACC;
+                        if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((tcount / C::NACC) & 1) ^ 1, kWaitLimitNs,
+                                                    abort_flag)) {
+                            timed_out();
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        issue(tmem_base + acc * C::ACC_COLS, C::IDESC, 0);
+                        ptx::mma_commit(&acc_full[acc]);
                     }
+                    if (!ok) break;
+                    // the stage's operands are free once the tile's MMAs are done
                     ptx::mma_commit(&empty_b[sb]);
-                    ptx::mma_commit(&acc_full[acc]);
                 }
                 if (ok) ptx::mma_commit(&a_empty[ab]);
             }
@@ -472,40 +513,47 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
         // ------------------------------------------------------------ epilogue (4 * EG warps)
         const int ew = warp - 2;             // 0 .. 4*EG-1
         const int quad = warp & 3;           // TMEM lane quadrant this warp may access
-        const int grp = ew >> 2;             // column group: columns [grp*BN/EG, (grp+1)*BN/EG)
+        const int grp = ew >> 2;             // epilogue group
         const int row = quad * 32 + lane;    // query row within the tile
-        constexpr int COLS = BN / EG;
-        constexpr int NCH = COLS / 32;
-        static_assert(COLS % 32 == 0, "column group must be whole 32-column chunks");
+        // RING: the group takes half tiles k with k mod EG = grp, i.e. half (grp & 1) of
+        // every STEP-th tile; otherwise columns [grp*WCOLS, (grp+1)*WCOLS) of every tile
+        const int half = grp & 1;
+        constexpr int STEP = C::RING ? EG / 2 : 1;
+        constexpr int WCOLS = C::WCOLS;
+        constexpr int NCH = WCOLS / 32;
+        const int col0 = C::RING ? half * WCOLS : grp * WCOLS;   // first point column of the visit
+        static_assert(WCOLS % 32 == 0 && (EG == 2 || EG == 4), "whole 32-column chunks");
         double *msum = reinterpret_cast<double *>(smem + C::OFF_MERGE);   // [EG-1][BM]
         double *mw = msum + (EG - 1) * BM;                                 // [EG-1][BM]
         float *mshift = reinterpret_cast<float *>(mw + (EG - 1) * BM);     // [EG-1][BM]
-        uint32_t tcount = 0, ucount = 0;
+        uint32_t tcount = 0, ucount = 0;  // point tiles and units this CTA has passed
         bool ok = true;
         RowState st{0.f, 0.f, 0.f, 0.f};
-        // One tile of this warp's columns: wait for its accumulator and row terms, sum
-        // the exponentials, release both, fold the sum into the row state. Returns false
-        // on timeout or abort.
-        auto tile = [&](auto masked, uint64_t kk2, int vcols) -> bool {
+        // This warp's columns of point tile number tc (CTA-wide count): wait for their
+        // accumulator and the tile's row terms, sum the exponentials, release both, fold
+        // the sum into the row state. Returns false on timeout or abort.
+        auto visit = [&](auto masked, uint64_t kk2, uint32_t tc, int vcols) -> bool {
             constexpr bool kMasked = decltype(masked)::value;
-            const int acc = tcount & 1;
-            const int ms = tcount % SMETA;
+            const uint32_t k = C::RING ? 2 * tc + half : tc;   // accumulator use, CTA-wide
+            const int acc = k % C::NACC;
+            const int ms = tc % SMETA;
             // lane 0 waits (the other lanes do not spend issue slots polling); the outcome
             // is broadcast so that the warp never splits around __syncwarp
             bool got = true;
             if (lane == 0)
-                got = ptx::mbar_wait_bounded(&acc_full[acc], (tcount >> 1) & 1, kWaitLimitNs, abort_flag) &&
-                      ptx::mbar_wait_bounded(&full_m[ms], (tcount / SMETA) & 1, kWaitLimitNs, abort_flag);
+                got = ptx::mbar_wait_bounded(&acc_full[acc], (k / C::NACC) & 1, kWaitLimitNs, abort_flag) &&
+                      ptx::mbar_wait_bounded(&full_m[ms], (tc / SMETA) & 1, kWaitLimitNs, abort_flag);
             if (!__shfl_sync(0xffffffffu, (int)got, 0)) return false;
             ptx::tc_fence_after();
             const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
             const float nb = -(meta[row] + st.shift);
             const float vrad = meta[BM];
             const uint64_t nb2 = pack2(nb, nb);
-            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + acc * BN + grp * COLS;
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(quad * 32) << 16) + acc * C::ACC_COLS + (C::RING ? 0 : grp * WCOLS);
             uint64_t acc_a = 0, acc_b = 0;  // {0.f, 0.f}
             auto release_acc = [&]() {
-                // every TMEM column of this buffer has been read: hand it back to the MMA
+                // every TMEM column of this accumulator has been read: hand it back
                 ptx::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&acc_empty[acc]);
@@ -559,7 +607,6 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             const float ts = (s0 + s1) + (s2 + s3);
             kahan_add(st.ksum, st.kc, ts);
             st.w32 = fmaf(ts, vrad, st.w32);
-            ++tcount;
             return true;
         };
         for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
@@ -572,14 +619,20 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             const int64_t t1 = min(T, t0 + I.tiles_per_split);
             const float kk = I.scales[2];
             const uint64_t kk2 = pack2(kk, kk);
-            // real points among this warp's columns of the point set's last tile
-            const int vlast = (int)max((int64_t)0, min((int64_t)COLS, I.n - (T - 1) * BN - grp * COLS));
-            const bool masked_end = t1 == T && vlast < COLS;
-            const int n_full = (int)(t1 - t0) - (masked_end ? 1 : 0);
+            const int ntiles = (int)(t1 - t0);
+            // this warp's tiles of the unit: i0, i0 + STEP, ... (by CTA-wide tile parity)
+            const uint32_t tbase = tcount;
+            const int i0 = (int)(((uint32_t)(grp >> 1) - tbase) & (uint32_t)(STEP - 1));
+            // real points among this warp's columns of the point set's last (padded) tile
+            const int vlast = (int)max((int64_t)0, min((int64_t)WCOLS, I.n - (T - 1) * BN - col0));
+            const bool mine_last = ntiles - 1 >= i0 && (ntiles - 1 - i0) % STEP == 0;
+            const bool masked_end = t1 == T && vlast < WCOLS && mine_last;
+            const int i_end = masked_end ? ntiles - 1 : ntiles;
             // the row's fixed shift: ceil of an upper bound on every exponent of the row
             st = RowState{ceilf(order_bits_to_float(I.ub[qt * BM + row])), 0.f, 0.f, 0.f};
-            for (int i = 0; i < n_full && ok; ++i) ok = tile(std::false_type{}, kk2, COLS);
-            if (ok && masked_end) ok = tile(std::true_type{}, kk2, vlast);
+            for (int i = i0; i < i_end && ok; i += STEP) ok = visit(std::false_type{}, kk2, tbase + i, WCOLS);
+            if (ok && masked_end) ok = visit(std::true_type{}, kk2, tbase + ntiles - 1, vlast);
+            tcount = tbase + ntiles;
             if (!ok) {
                 timed_out();
                 break;
