@@ -127,7 +127,7 @@ struct Geo {
     static constexpr uint32_t SW = CW == 16 ? ptx::kSw32 : (CW == 32 ? ptx::kSw64 : ptx::kSw128);
     static constexpr uint32_t SBO = 8 * CW * 2;        // bytes between 8-row core-matrix groups
     // byte offset of MMA K-step s inside a plane of `rows` rows
-    __device__ static uint32_t koff(int s, int rows) {
+    __host__ __device__ static constexpr uint32_t koff(int s, int rows) {
         return (uint32_t)((s / SPC) * rows * CW * 2 + (s % SPC) * 32);
     }
 };
@@ -441,6 +441,8 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 }
                 ptx::tc_fence_after();
                 const uint32_t abase = a0 + ab * C::A_BYTES;
+                const uint32_t alo = ptx::smem_desc_lo(abase, 16);
+                const uint32_t alo_aug = ptx::smem_desc_lo(abase + 2 * C::A_PLANE, 16);
                 for (int64_t t = t0; t < t1 && ok; ++t, ++tcount) {
                     const int sb = tcount % SB;
                     if (!ptx::mbar_wait_bounded(&full_b[sb], (tcount / SB) & 1, kWaitLimitNs, abort_flag)) {
@@ -450,26 +452,32 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                     }
                     ptx::tc_fence_after();
                     const uint32_t bbase = b0 + sb * C::B_BYTES;
-                    // 3 * K/16 + 1 MMAs: the split products, then the point term
-                    auto issue = [&](uint32_t d_tmem, uint32_t idesc, uint32_t row0) {
+                    // 3 * K/16 + 1 MMAs: the split products, then the point term. Each operand's
+                    // descriptor is the stage's base low word plus a compile-time constant and a
+                    // constant high word, so the single issuing thread (which shares its
+                    // scheduler with epilogue warps) spends one add per operand: at K = 16 the
+                    // MMAs of a half tile are short and issue cost decides the pipe's rate.
+                    const uint32_t blo = ptx::smem_desc_lo(bbase, 16);
+                    const uint32_t blo_aug = ptx::smem_desc_lo(bbase + 2 * C::B_PLANE, 16);
+                    constexpr uint32_t HI = ptx::smem_desc_hi(G::SBO, G::SW);
+                    constexpr uint32_t HI_AUG = ptx::smem_desc_hi(256, ptx::kSw32);
+                    auto issue = [&](uint32_t d_tmem, uint32_t row0) {
                         uint32_t accumulate = 0;
 #pragma unroll
                         for (int prod = 0; prod < 3; ++prod) {
                             // (u_hi, v_hi), (u_hi, v_lo), (u_lo, v_hi); B rows row0..
-                            const uint32_t ap = abase + (prod == 2 ? C::A_PLANE : 0);
-                            const uint32_t bp = bbase + (prod == 1 ? C::B_PLANE : 0) + row0 * G::CW * 2;
 #pragma unroll
                             for (int s = 0; s < KP / 16; ++s) {
-                                const uint64_t ad = ptx::smem_desc(ap + G::koff(s, BM), 16, G::SBO, G::SW);
-                                const uint64_t bd = ptx::smem_desc(bp + G::koff(s, BN), 16, G::SBO, G::SW);
-                                ptx::mma_f16(d_tmem, ad, bd, idesc, accumulate);
+                                const uint32_t aoff = (prod == 2 ? C::A_PLANE : 0) + G::koff(s, BM);
+                                const uint32_t boff =
+                                    (prod == 1 ? C::B_PLANE : 0) + row0 * G::CW * 2 + G::koff(s, BN);
+                                ptx::mma_f16_w(d_tmem, alo + (aoff >> 4), HI, blo + (boff >> 4), HI, C::IDESC,
+                                               accumulate);
                                 accumulate = 1;
                             }
                         }
                         // constant A column x (-g/2) pieces, one K = 16 step
-                        const uint64_t ad = ptx::smem_desc(abase + 2 * C::A_PLANE, 16, 256, ptx::kSw32);
-                        const uint64_t bd = ptx::smem_desc(bbase + 2 * C::B_PLANE + row0 * 32, 16, 256, ptx::kSw32);
-                        ptx::mma_f16(d_tmem, ad, bd, idesc, 1);
+                        ptx::mma_f16_w(d_tmem, alo_aug, HI_AUG, blo_aug + ((row0 * 32) >> 4), HI_AUG, C::IDESC, 1);
                     };
                     if constexpr (C::RING) {
 #pragma unroll
@@ -483,7 +491,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                                 break;
                             }
                             ptx::tc_fence_after();
-                            issue(tmem_base + acc * C::ACC_COLS, C::IDESC, h * C::ACC_COLS);
+                            issue(tmem_base + acc * C::ACC_COLS, h * C::ACC_COLS);
                             ptx::mma_commit(&acc_full[acc]);
                         }
                     } else {
@@ -495,7 +503,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                             break;
                         }
                         ptx::tc_fence_after();
-                        issue(tmem_base + acc * C::ACC_COLS, C::IDESC, 0);
+                        issue(tmem_base + acc * C::ACC_COLS, 0);
                         ptx::mma_commit(&acc_full[acc]);
                     }
                     if (!ok) break;
