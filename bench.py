@@ -46,7 +46,11 @@ WORKLOADS = {
     "large_d64": "exact Gaussian KDE n=2000000 m=100000 d=64 FP32, 50-component mixture means U[-10,10]^64 std logU[0.5,2], a=0.05",
     "batched": "256 KDE instances, n logU[1000,200000], m logU[64,8192], d in {8,32,128}, a U[0.01,1], 10-component mixtures means U[-10,10]^d std 1, one batched call per step (graph replay)",
     "serving": "8 resident datasets n log-spaced 1e4..2e6, d in {2,4,8,16,32,64,96,128}, a=1/d; Poisson arrivals, m logU[1,4096], random dataset; loads 0.3/0.6/0.9 x saturation",
+    "kernels": "exact KDE with the exponential exp(-a r) and logistic 4/(2+e^{ar}+e^{-ar}) kernels, n=m=100000 d=16 FP32 (the single_d16 mixture), a=0.3, plain FP32 form",
+    "subset": "weighted subset sums (random-sampling estimator): n=1000000 d=16 FP32 points (single_d16 mixture), m=100000 queries, 1000 uniform candidates each with weight n/1000, Gaussian a=0.1",
 }
+KERNELS_OF = {"kernels": ["exponential", "logistic"]}
+SUBSET_N, SUBSET_M, SUBSET_L = 1_000_000, 100_000, 1000
 
 
 def build_workload(name, rank=0, n=None, m=None):
@@ -55,6 +59,9 @@ def build_workload(name, rank=0, n=None, m=None):
         if rank:
             Q = G.sample(G.make_mixture(0, 10, 16, -10.0, 10.0, 1.0), 1000 + rank, Q.shape[0], "query")
         return X, Q, [0.01, 0.1, 1.0]
+    if name == "kernels":
+        X, Q = G.workload_single_d16(0, n or 100_000, m or 100_000)
+        return X, Q, [0.3, 0.3]
     if name == "large_d64":
         X, Q, a = G.workload_large_d64(0, n or 2_000_000, m or 100_000)
         if rank:
@@ -121,21 +128,22 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------
 # CPU baseline (the FP64 oracle, as it stands)
 # ------------------------------------------------------------------------------------
-def cpu_oracle_rate(X, Q, a, budget_s=12.0, min_q=2):
+def cpu_oracle_rate(X, Q, a, budget_s=12.0, min_q=2, kernel="gaussian"):
     import oracle
     threads = os.cpu_count() or 1
     q0 = max(min_q, threads)
     t = time.perf_counter()
-    oracle.kde(X, Q[:q0], a, threads=threads)
+    oracle.kde_kernel(X, Q[:q0], a, kernel, threads=threads)
     dt = time.perf_counter() - t
     per_q = dt / q0
     s = int(min(len(Q), max(q0, budget_s / max(per_q, 1e-9))))
     s = max(threads, (s // threads) * threads) if s >= threads else s
     t = time.perf_counter()
-    oracle.kde(X, Q[:s], a, threads=threads)
+    oracle.kde_kernel(X, Q[:s], a, kernel, threads=threads)
     dt = time.perf_counter() - t
     return {"value": s * X.shape[0] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {s} queries x all {X.shape[0]} points, d={X.shape[1]}, a={a}, FP64, {dt:.1f} s"}
+            "sample": f"first {s} queries x all {X.shape[0]} points, d={X.shape[1]}, a={a}, {kernel} kernel, FP64, "
+                      f"{dt:.1f} s"}
 
 
 def run_reference(args):
@@ -143,6 +151,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
+    if args.workload == "subset":
+        return run_reference_subset(args)
     if args.workload in ("batched", "serving"):
         # a bounded sample: the first instances of the batched workload
         inst = build_batched(6)
@@ -150,18 +160,19 @@ def run_reference(args):
         alist = [a0]
     else:
         X, Q, alist = build_workload(args.workload)
+    kernels = KERNELS_OF.get(args.workload, ["gaussian"] * len(alist))
     threads = os.cpu_count() or 1
     # size each step so that warmup + steps stay within a few minutes
     budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
     per = cpu_oracle_rate(X, Q, alist[0], budget_s=1.0)
     s = int(max(threads, min(len(Q), budget * per["value"] / X.shape[0] / len(alist))))
     for _ in range(args.warmup):
-        for a in alist:
-            oracle.kde(X, Q[:threads], a, threads=threads)
+        for a, kn in zip(alist, kernels):
+            oracle.kde_kernel(X, Q[:threads], a, kn, threads=threads)
     t = time.perf_counter()
     for _ in range(args.steps):
-        for a in alist:
-            oracle.kde(X, Q[:s], a, threads=threads)
+        for a, kn in zip(alist, kernels):
+            oracle.kde_kernel(X, Q[:s], a, kn, threads=threads)
     dt = time.perf_counter() - t
     value = args.steps * len(alist) * s * X.shape[0] / dt
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
@@ -171,6 +182,50 @@ def run_reference(args):
                                              "sample_queries_per_step": s, "bandwidths": alist},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{s} queries x {X.shape[0]} points per bandwidth per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def build_subset(seed=3):
+    """The subset workload: points, queries, CSR lists (uniform candidates) and weights."""
+    X, Q = G.workload_single_d16(0, SUBSET_N, SUBSET_M)
+    r = np.random.default_rng(seed)
+    idx = r.integers(0, SUBSET_N, size=SUBSET_M * SUBSET_L, dtype=np.int64)
+    off = np.arange(0, (SUBSET_M + 1) * SUBSET_L, SUBSET_L, dtype=np.int64)
+    W = np.full(len(idx), SUBSET_N / SUBSET_L, dtype=np.float32)
+    return X, Q, off, idx, W, 0.1
+
+
+def subset_oracle_rate(X, Q, off, idx, W, a, budget_s):
+    import oracle
+    threads = os.cpu_count() or 1
+    L_ = int(off[1] - off[0])
+
+    def run(q):
+        return oracle.kde_subset(X, Q[:q], a, off[:q + 1], idx[:q * L_], W[:q * L_], threads=threads)
+    q0 = max(threads, 64)
+    t = time.perf_counter()
+    run(q0)
+    per_q = (time.perf_counter() - t) / q0
+    s = int(min(len(Q), max(q0, budget_s / max(per_q, 1e-12))))
+    t = time.perf_counter()
+    run(s)
+    dt = time.perf_counter() - t
+    return {"value": s * L_ / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {s} queries x {L_} list entries, d={X.shape[1]}, a={a}, FP64, {dt:.1f} s"}
+
+
+def run_reference_subset(args):
+    X, Q, off, idx, W, a = build_subset()
+    budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    rates = [subset_oracle_rate(X, Q, off, idx, W, a, budget) for _ in range(args.warmup + args.steps)]
+    value = statistics.median(r["value"] for r in rates[args.warmup:])
+    cpu = dict(rates[-1], value=value)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS["subset"]}, "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -266,10 +321,11 @@ def run_gpu(args):
     lib = L.load()
 
     X, Q, alist = build_workload(args.workload, rank, args.n, args.m)
+    kernels = KERNELS_OF.get(args.workload, ["gaussian"] * len(alist))
     n, d = X.shape
     m = Q.shape[0]
     t = time.perf_counter()
-    kdes = [ExactGaussianKDE(X, a, form=args.form) for a in alist]
+    kdes = [ExactGaussianKDE(X, a, form=args.form, kernel=kn) for a, kn in zip(alist, kernels)]
     torch.cuda.synchronize()
     create_ms = 1e3 * (time.perf_counter() - t) / len(alist)
     form = kdes[0].form
@@ -363,7 +419,8 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(X, Q, alist[len(alist) // 2], budget_s=args.cpu_budget)
+        cpu = cpu_oracle_rate(X, Q, alist[len(alist) // 2], budget_s=args.cpu_budget,
+                              kernel=kernels[len(alist) // 2])
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -371,7 +428,7 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if form != "simt_f64" else "f64",
                 "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.workload], "n": n, "m": m, "d": d, "bandwidths": alist,
-                           "form": form, "l2": "flushed between steps (512 MiB write)",
+                           "kernels": kernels, "form": form, "l2": "flushed between steps (512 MiB write)",
                            "parallelism": f"replicas x{world} (query batches)"},
                 "create_ms": create_ms, "autotune_s": tune_s, "gpu_launches": int(launches), "roofline": roof,
                 "recomputed_fp32_queries": recomputed,
@@ -380,6 +437,114 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     for k in kdes:
         k.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_subset(args):
+    """Subset workload: one weighted-subset call (10^8 list entries) per step."""
+    import torch
+    import torch.distributed as dist
+    from paper_2407_07096_gb300 import build as B
+    from paper_2407_07096_gb300 import _lib as L
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    lib = L.load()
+    X, Q, off, idx, W, a = build_subset(3 + rank)
+    n, d = X.shape
+    m = Q.shape[0]
+    entries = int(off[-1])
+    t = time.perf_counter()
+    kde = ExactGaussianKDE(X, a, form="simt_f32")  # subset sums gather from the plain form's points
+    torch.cuda.synchronize()
+    create_ms = 1e3 * (time.perf_counter() - t)
+    Qd, offd = torch.from_numpy(Q).to(dev), torch.from_numpy(off).to(dev)
+    idxd, Wd = torch.from_numpy(idx).to(dev), torch.from_numpy(W).to(dev)
+    out = torch.empty(m, dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            kde.query_subset_dev(Qd, offd, idxd, Wd, out, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = lib.stag_kde_launch_count()
+    for i in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            ev[i][0].record(stream)
+            kde.query_subset_dev(Qd, offd, idxd, Wd, out, stream)
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = lib.stag_kde_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [x.elapsed_time(y) for x, y in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t_all = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        total_ms = float(t_all.item())
+    value = world * entries * args.steps / (total_ms * 1e-3)
+    # end to end through the host entry point (pinned buffers in and out)
+    pin = [torch.from_numpy(x).pin_memory().numpy() for x in (Q, off, idx, W)]
+    e2e_steps = max(1, min(args.steps, 5))
+    kde.query_subset(*pin)
+    if world > 1:
+        dist.barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        kde.query_subset(*pin)
+    e2e_s = time.perf_counter() - t
+    if world > 1:
+        t_all = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+        e2e_s = float(t_all.item())
+    e2e = {"value": world * entries * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(x.nbytes for x in pin)), "d2h_bytes_per_step": int(m * 8),
+           "steps": e2e_steps}
+    # roofline: the launch's compulsory HBM bytes (index and weight streams, queries,
+    # offsets, results, the point set once) against the measured copy bandwidth; the row
+    # gathers (entries x 4d bytes) are reported beside it, since X (4nd bytes) fits in L2
+    peaks, peak_kind = load_peaks()
+    kern_ms = statistics.median(step_ms)
+    algo = entries * 12 + m * (4 * d + 8 + 8) + 4 * n * d
+    gathered = entries * 4 * d
+    roof = {"bound": "hbm", "achieved": algo / (kern_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": algo / (kern_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], "traffic": None,
+            "algorithmic_bytes": algo, "gathered_row_bytes": gathered,
+            "gather_gbs": (algo + gathered) / (kern_ms * 1e-3) / 1e9, "peak_source": peak_kind,
+            "kernel_ms_per_launch": kern_ms,
+            "note": "per launch: 12 B/entry index+weight, queries, offsets, results, X once; rows gathered "
+                    "from L2 (X = 64 MB) are in gather_gbs"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = subset_oracle_rate(X, Q, off, idx, W, a, args.cpu_budget)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["subset"], "n": n, "m": m, "d": d, "list_length": SUBSET_L,
+                           "bandwidths": [a], "l2": "flushed between steps (512 MiB write)",
+                           "parallelism": f"replicas x{world} (query batches)"},
+                "create_ms": create_ms, "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu,
+                "e2e": e2e, "clocks": clk,
+                "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}
+        print(json.dumps(line), flush=True)
+    kde.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -581,6 +746,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "subset":
+        return run_subset(args)
     if args.workload == "serving":
         return run_serving(args)
     return run_gpu(args)

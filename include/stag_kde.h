@@ -52,6 +52,21 @@ extern "C" {
 #define STAG_KDE_F32 0
 #define STAG_KDE_F64 1
 
+/*
+ * Kernel function k of the distance r = ||q - x|| (Sec. 3 lists three):
+ *   GAUSSIAN     k = exp(-a r^2)                       (the default; every form)
+ *   EXPONENTIAL  k = exp(-a r)                         (plain FP32 and FP64 forms)
+ *   LOGISTIC     k = 4 / (2 + exp(a r) + exp(-a r))    (plain FP32 and FP64 forms)
+ * The paper writes the logistic kernel without a bandwidth; here its argument is a*r, so
+ * a = 1 gives the paper's k(r). The tensor-core form serves only the Gaussian kernel: the
+ * other two take sqrt of the squared distance, which turns the split products' absolute
+ * error in r^2 into a large relative error near r = 0. AUTO picks the plain FP32 form
+ * for them; an explicit STAG_KDE_FORM_TC returns STAG_KDE_EUNSUPPORTED.
+ */
+#define STAG_KDE_KERNEL_GAUSSIAN 0
+#define STAG_KDE_KERNEL_EXPONENTIAL 1
+#define STAG_KDE_KERNEL_LOGISTIC 2
+
 /* Evaluation form ("precision form"). */
 #define STAG_KDE_FORM_AUTO 0     /* library picks (tensor-core form where its error model allows) */
 #define STAG_KDE_FORM_SIMT_F32 1 /* plain FP32 CUDA-core kernel, direct differences              */
@@ -67,10 +82,11 @@ typedef struct stag_kde_opts {
     int tc_no_check;/* tensor-core form only. 0 (default): every query gets an error   *
                      * estimate; those above 7.5e-5 relative are recomputed with the    *
                      * plain FP32 form. 1: skip the estimate and keep every result.     */
-    int reserved[4];/* must be zero                                                   */
+    int kernel;     /* STAG_KDE_KERNEL_*; 0 = Gaussian                                */
+    int reserved[3];/* must be zero                                                   */
 } stag_kde_opts;
 
-/* Fills *o with the defaults (AUTO form, unnormalised, current device). */
+/* Fills *o with the defaults (AUTO form, unnormalised, current device, Gaussian kernel). */
 void stag_kde_opts_init(stag_kde_opts *o);
 
 /*
@@ -106,6 +122,36 @@ int stag_kde_query(stag_kde_t *h, const void *Q, int64_t m, double *out);
  * nothing for m <= the reserved size.
  */
 int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, void *stream);
+
+/*
+ * Weighted subset sums, the estimator that random sampling (every sampled point
+ * weighted n/s) and the CKNS scheme (weights 2^i on hashed candidates) evaluate
+ * (Sec. 3.1): for every query j, over its own list of (point index, weight) pairs,
+ *     out[j] = sum_{p = off[j] .. off[j+1]-1} W[p] k(||q_j - x_{idx[p]}||)
+ * (times 1/n when the handle normalises), in the handle's kernel function k. Q is
+ * m x d FP32; off has m + 1 entries (off[0] = 0, non-decreasing; query j owns entries
+ * off[j] .. off[j+1]-1, an empty list gives 0); idx has off[m] entries, each a row of X
+ * as given at create (repeats allowed); W has off[m] weights, or NULL for all 1. Each
+ * term is evaluated in FP32 by direct differences (the plain form's arithmetic, so the
+ * same error bound) with a per-query power-of-two shift and FP64 accumulation. FP32
+ * handles of any form (the point set is gathered from a row-major copy built on the
+ * first call); FP64 handles return STAG_KDE_EUNSUPPORTED.
+ *
+ * Host variant: all buffers in host memory, synchronous; validates everything first
+ * (offsets, indices in [0, n), finite W >= 0, finite Q) and returns STAG_KDE_EINVAL on a
+ * violation with out untouched.
+ */
+int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_t *off, const int64_t *idx,
+                          const float *W, double *out);
+
+/*
+ * Device variant: dQ, dOff, dIdx, dW (or NULL) and dOut are device pointers on the
+ * handle's device; work is queued on `stream` (a cudaStream_t) and the call returns.
+ * Only pointers and m are validated; an entry whose index lies outside [0, n)
+ * contributes nothing, and offsets must satisfy the host variant's rules (not checked).
+ */
+int stag_kde_query_subset_dev(stag_kde_t *h, const float *dQ, int64_t m, const int64_t *dOff, const int64_t *dIdx,
+                              const float *dW, double *dOut, void *stream);
 
 /*
  * Batched evaluation: instance i evaluates the device query matrix dQs[i] (ms[i] rows,
@@ -161,6 +207,11 @@ void stag_kde_destroy(stag_kde_t *h);
 
 /* Thread-local description of the calling thread's last failure ("" if none). */
 const char *stag_kde_last_error(void);
+
+/* Thread-local STAG_KDE_E* code of the calling thread's last failure (0 if none): the
+ * code behind a NULL from stag_kde_create / stag_kde_create_ex / stag_srv_start.
+ * Failures that only set a message (argument checks) report STAG_KDE_EINVAL. */
+int stag_kde_last_error_code(void);
 
 /* Library version string. */
 const char *stag_kde_version(void);

@@ -45,7 +45,11 @@ def _load():
             lib.oracle_kde_weighted.argtypes = [_D, _D, i64, _D, i64, i64, dbl, _D, c_int]
             lib.oracle_kde_self.argtypes = [_D, i64, i64, dbl, _D, c_int]
             lib.oracle_kde_log.argtypes = [_D, i64, _D, i64, i64, dbl, _D, _D, _D, c_int]
-            for f in (lib.oracle_kde, lib.oracle_kde_weighted, lib.oracle_kde_self, lib.oracle_kde_log):
+            lib.oracle_kde_kernel.argtypes = [c_int, _D, i64, _D, i64, i64, dbl, _D, c_int]
+            _I = ctypes.POINTER(ctypes.c_int64)
+            lib.oracle_kde_subset.argtypes = [c_int, _D, i64, _D, i64, i64, dbl, _I, _I, _D, _D, c_int]
+            for f in (lib.oracle_kde, lib.oracle_kde_weighted, lib.oracle_kde_self, lib.oracle_kde_log,
+                      lib.oracle_kde_kernel, lib.oracle_kde_subset):
                 f.restype = c_int
             _lib = lib
     return _lib
@@ -94,6 +98,43 @@ def kde_weighted(X, W, Q, a: float, threads: int | None = None) -> np.ndarray:
                                      float(a), _p(out), _threads(threads))
     if rc:
         raise ValueError("oracle_kde_weighted rejected its arguments")
+    return out
+
+
+KERNELS = {"gaussian": 0, "exponential": 1, "logistic": 2}
+
+
+def kde_kernel(X, Q, a: float, kernel: str = "gaussian", threads: int | None = None) -> np.ndarray:
+    """sum_i k(||q - x_i||) in FP64 for the kernel functions of Sec. 3: "gaussian"
+    exp(-a r^2), "exponential" exp(-a r), "logistic" 4 / (2 + exp(a r) + exp(-a r))."""
+    X, Q = _check(X, Q)
+    out = np.empty(Q.shape[0], dtype=np.float64)
+    rc = _load().oracle_kde_kernel(KERNELS[kernel], _p(X), X.shape[0], _p(Q), Q.shape[0], X.shape[1],
+                                   float(a), _p(out), _threads(threads))
+    if rc:
+        raise ValueError(f"oracle_kde_kernel failed ({rc})")
+    return out
+
+
+def kde_subset(X, Q, a: float, offsets, idx, W=None, kernel: str = "gaussian",
+               threads: int | None = None) -> np.ndarray:
+    """out_j = sum over query j's list entries p = offsets[j] .. offsets[j+1]-1 of
+    W[p] k(||q_j - x_{idx[p]}||) (W = None: weights 1), in list order (Sec. 3.1)."""
+    X, Q = _check(X, Q)
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+    if off.shape != (Q.shape[0] + 1,) or ix.shape != (int(off[-1]) if len(off) else 0,):
+        raise ValueError("offsets must have m + 1 entries and idx offsets[-1]")
+    w = None if W is None else _f64(W)
+    if w is not None and w.shape != ix.shape:
+        raise ValueError("W must match idx")
+    out = np.empty(Q.shape[0], dtype=np.float64)
+    I = ctypes.POINTER(ctypes.c_int64)
+    rc = _load().oracle_kde_subset(KERNELS[kernel], _p(X), X.shape[0], _p(Q), Q.shape[0], X.shape[1], float(a),
+                                   off.ctypes.data_as(I), ix.ctypes.data_as(I), None if w is None else _p(w),
+                                   _p(out), _threads(threads))
+    if rc:
+        raise ValueError(f"oracle_kde_subset failed ({rc})")
     return out
 
 

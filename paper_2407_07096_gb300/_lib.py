@@ -20,6 +20,8 @@ F32, F64 = 0, 1
 FORM_AUTO, FORM_SIMT_F32, FORM_TC, FORM_SIMT_F64 = 0, 1, 2, 3
 FORM_NAMES = {FORM_AUTO: "auto", FORM_SIMT_F32: "simt_f32", FORM_TC: "tc", FORM_SIMT_F64: "simt_f64"}
 FORMS = {v: k for k, v in FORM_NAMES.items()}
+KERNEL_GAUSSIAN, KERNEL_EXPONENTIAL, KERNEL_LOGISTIC = 0, 1, 2
+KERNELS = {"gaussian": KERNEL_GAUSSIAN, "exponential": KERNEL_EXPONENTIAL, "logistic": KERNEL_LOGISTIC}
 
 
 class StagKdeError(RuntimeError):
@@ -36,7 +38,7 @@ class SrvOpts(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int), ("normalise", ctypes.c_int), ("device", ctypes.c_int),
-                ("tc_no_check", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("tc_no_check", ctypes.c_int), ("kernel", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 # (name, restype, argtypes) for every entry point declared in include/stag_kde.h
@@ -47,6 +49,8 @@ SIGNATURES = [
     ("stag_kde_create_ex", _VP, [_VP, _INT, _I64, _I64, _DBL, ctypes.POINTER(Opts)]),
     ("stag_kde_query", _INT, [_VP, _VP, _I64, _VP]),
     ("stag_kde_query_dev", _INT, [_VP, _VP, _I64, _VP, _VP]),
+    ("stag_kde_query_subset", _INT, [_VP, _VP, _I64, _VP, _VP, _VP, _VP]),
+    ("stag_kde_query_subset_dev", _INT, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     ("stag_kde_reserve", _INT, [_VP, _I64]),
     ("stag_kde_query_batch", _INT, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_I64),
                                     ctypes.POINTER(_VP), _I64, _VP]),
@@ -57,6 +61,7 @@ SIGNATURES = [
     ("stag_kde_destroy", None, [_VP]),
     ("stag_kde_last_recomputed", _INT, [_VP, ctypes.POINTER(_I64)]),
     ("stag_kde_last_error", ctypes.c_char_p, []),
+    ("stag_kde_last_error_code", _INT, []),
     ("stag_kde_version", ctypes.c_char_p, []),
     ("stag_kde_launch_count", ctypes.c_uint64, []),
     ("stag_kde_profile_begin", _INT, [_VP]),

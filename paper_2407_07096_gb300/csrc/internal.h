@@ -58,6 +58,7 @@ struct stag_kde {
     int dtype = STAG_KDE_F32;
     int form = STAG_KDE_FORM_SIMT_F32;
     int normalise = 0;
+    int kernel = STAG_KDE_KERNEL_GAUSSIAN;  // k(r): Gaussian, exponential or logistic
     bool tc_check = true;  // recompute queries the tensor-core error estimate flags
     uint64_t scratch_epoch = 0;    // bumped whenever scratch is reallocated (graphs hold pointers)
     bool is_view = false;          // shares another handle's point-set data (serving slots)
@@ -84,6 +85,9 @@ struct stag_kde {
     double *out_dev = nullptr;
     int64_t out_cap = 0;  // bytes
     stagkde::Partials part;
+    float *xrow = nullptr;    // row-major FP32 point set for gathers (subset sums), built on first use
+    void *sub_dev = nullptr;  // host subset call: device copies of offsets, indices, weights
+    int64_t sub_dev_cap = 0;  // bytes
     int *flag_dev = nullptr;  // input-validation flag
     int *flag_host = nullptr; // pinned mirror
     int sm_count = 0;
@@ -121,6 +125,12 @@ int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, con
 int ensure_qt(stag_kde *h, int64_t floats);
 int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s);
 int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s);
+
+// kde_subset.cu: weighted subset sums over per-query (index, weight) lists. `entries`
+// (the list entries, if known on the host) only feeds the profiling counters.
+int subset_prepare(stag_kde *h, cudaStream_t s);
+int subset_query(stag_kde *h, const float *dQ, int64_t m, const int64_t *dOff, const int64_t *dIdx, const float *dW,
+                 double *dOut, cudaStream_t s, double entries);
 
 // kde_combine.cu
 int launch_combine(const double *part_sum, const float *part_shift, int64_t m, int splits,

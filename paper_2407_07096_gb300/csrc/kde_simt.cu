@@ -1,5 +1,6 @@
-// Plain CUDA-core forms of exact Gaussian KDE (Sec. 3: K(q) = sum_i exp(-a ||q - x_i||^2),
-// evaluated over every data point, the "naive" exact method of Sec. 3 / Sec. 6.1).
+// Plain CUDA-core forms of exact KDE (Sec. 3: K(q) = sum_i k(||q - x_i||), by default the
+// Gaussian kernel k(r) = exp(-a r^2); also the exponential and logistic kernels of Sec. 3),
+// evaluated over every data point, the "naive" exact method of Sec. 3 / Sec. 6.1.
 //
 //  * kde_simt_f32_kernel: FP32 direct differences sum_k (q_k - x_k)^2, register-tiled
 //    4 queries x 4 points per thread, 64 x 64 pairs per 256-thread block, shared-memory
@@ -17,6 +18,9 @@
 // the row's accumulators by the exact power of two 2^(s_old - s_new). Terms more than
 // 2^-126 below the shift flush to zero (relative contribution < n 2^-126).
 //
+// Other kernel functions (Sec. 3): the exponential and logistic kernels of r = sqrt(d2),
+// in the same shifted form (kernel_fn.cuh).
+//
 // Summation: per thread, FP32 over 16 tiles (64 terms), then FP64; the 16 threads that
 // share a row are combined in FP64 with a fixed shuffle pattern; splits of the point set
 // are combined in FP64 by kde_combine.cu. Every order is fixed, so results are
@@ -25,6 +29,7 @@
 
 #include "f32x2.cuh"
 #include "internal.h"
+#include "kernel_fn.cuh"
 
 namespace stagkde {
 
@@ -33,12 +38,6 @@ namespace {
 constexpr float kShiftFloor = -0x1p100f;  // initial shift (an exact integer)
 constexpr float kOverflowGuard = 0x1p64f;
 constexpr int kFlushTiles = 16;
-
-__device__ __forceinline__ float ex2_approx(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -68,25 +67,29 @@ __device__ __forceinline__ void rescale(RowAcc &r, float s_new) {
     r.shift = s_new;
 }
 
-// Adds the four terms 2^(negc*d2[j] - shift) (j < valid) to row r.
+using kfn::term;
+using kfn::term_log2;
+
+// Adds the four terms k(r_j) 2^-shift (j < valid) to row r.
+template <int KERN>
 __device__ __forceinline__ void add_terms(RowAcc &r, const float d2[4], float negc, int valid) {
     float ts = 0.f;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float e = ex2_approx(fmaf(negc, d2[j], -r.shift));
+        float e = term<KERN>(negc, d2[j], r.shift);
         ts += (j < valid) ? e : 0.f;
     }
     if (!(ts <= kOverflowGuard)) {
         float mx = -INFINITY;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
-            if (j < valid) mx = fmaxf(mx, negc * d2[j]);
+            if (j < valid) mx = fmaxf(mx, term_log2<KERN>(negc, d2[j]));
         float s_new = fmaxf(ceilf(mx), kShiftFloor);
         if (s_new > r.shift) rescale(r, s_new);
         ts = 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float e = ex2_approx(fmaf(negc, d2[j], -r.shift));
+            float e = term<KERN>(negc, d2[j], r.shift);
             ts += (j < valid) ? e : 0.f;
         }
     }
@@ -102,7 +105,7 @@ __device__ __forceinline__ void merge(RowAcc &r, double oacc, float oshift) {
 // One work item: query tile `qtile` (64 rows) against the point tiles of range `split`.
 // Rows at or past m_real are computed on zero padding and not stored; partials use the
 // row stride m.
-template <bool kSingleChunk>
+template <bool kSingleChunk, int KERN>
 __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], float (*sQ)[kSimtKC * kSimtTile],
                                           const float *__restrict__ xt, int64_t n, int64_t n_tiles,
                                           const float *__restrict__ qt, int64_t m, int64_t m_real, int d_pad,
@@ -186,7 +189,7 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
                 float d2[4];
                 f2::unpack(d2p[i][0], d2[0], d2[1]);
                 f2::unpack(d2p[i][1], d2[2], d2[3]);
-                add_terms(row[i], d2, negc, valid);
+                add_terms<KERN>(row[i], d2, negc, valid);
                 d2p[i][0] = d2p[i][1] = 0ull;
             }
             if (++group == kFlushTiles) {
@@ -227,7 +230,7 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
     }
 }
 
-template <bool kSingleChunk>
+template <bool kSingleChunk, int KERN>
 __global__ void __launch_bounds__(256, 2)
 kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, const float *__restrict__ qt, int64_t m,
                     int d_pad, float negc, int64_t tiles_per_split, int64_t splits, double *__restrict__ part_sum,
@@ -236,8 +239,8 @@ kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, co
     __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
     if (!count) {
         // one block per (query tile, split)
-        simt_item<kSingleChunk>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum, part_shift,
-                                blockIdx.x, blockIdx.y);
+        simt_item<kSingleChunk, KERN>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum,
+                                      part_shift, blockIdx.x, blockIdx.y);
         return;
     }
     // `count` (device memory): only the first *count query rows are real; a fixed grid
@@ -246,8 +249,8 @@ kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, co
     const int64_t items = ((rows + kSimtTile - 1) / kSimtTile) * splits;
     for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
         __syncthreads();  // the previous item's shared-memory reads are done
-        simt_item<kSingleChunk>(sX, sQ, xt, n, n_tiles, qt, m, rows, d_pad, negc, tiles_per_split, part_sum,
-                                part_shift, w / splits, w % splits);
+        simt_item<kSingleChunk, KERN>(sX, sQ, xt, n, n_tiles, qt, m, rows, d_pad, negc, tiles_per_split, part_sum,
+                                      part_shift, w / splits, w % splits);
     }
 }
 
@@ -284,7 +287,7 @@ __global__ void check_finite_kernel(const T *__restrict__ p, int64_t count, int 
 // index order with FP64 exp (plain double arithmetic, for FP64 inputs).
 __global__ void __launch_bounds__(128)
 kde_simt_f64_kernel(const double *__restrict__ X, int64_t n, const double *__restrict__ Q,
-                    int64_t m, int64_t d, double a, double *__restrict__ out) {
+                    int64_t m, int64_t d, double a, int kern, double *__restrict__ out) {
     extern __shared__ double sx[];
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t tp = max((int64_t)1, (int64_t)(4096 / d));  // points per staged tile
@@ -302,7 +305,12 @@ kde_simt_f64_kernel(const double *__restrict__ X, int64_t n, const double *__res
                     const double t = q[k] - sx[i * d + k];
                     d2 = fma(t, t, d2);
                 }
-                s += exp(-a * d2);
+                if (kern == STAG_KDE_KERNEL_GAUSSIAN) {
+                    s += exp(-a * d2);
+                } else {
+                    const double x = a * sqrt(d2);
+                    s += kern == STAG_KDE_KERNEL_EXPONENTIAL ? exp(-x) : 4.0 / (2.0 + exp(x) + exp(-x));
+                }
             }
         }
     }
@@ -397,6 +405,30 @@ int simt_prepare_points(stag_kde *h, const float *dX) {
     return 0;
 }
 
+// Launches the FP32 kernel instance for the handle's operand width and kernel function.
+template <int KERN>
+void launch_simt_kern(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, float negc, int64_t tps,
+                      int64_t splits, const int *count) {
+    if (h->d_pad <= kSimtKC)
+        kde_simt_f32_kernel<true, KERN><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
+                                                             splits, h->part.sum, h->part.shift, count);
+    else
+        kde_simt_f32_kernel<false, KERN><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
+                                                              splits, h->part.sum, h->part.shift, count);
+}
+void launch_simt(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, int64_t tps, int64_t splits,
+                 const int *count) {
+    const float negc = (float)(-h->a * 1.4426950408889634);  // -a log2(e)
+    switch (h->kernel) {
+        case STAG_KDE_KERNEL_EXPONENTIAL:
+            return launch_simt_kern<STAG_KDE_KERNEL_EXPONENTIAL>(h, grid, s, m, negc, tps, splits, count);
+        case STAG_KDE_KERNEL_LOGISTIC:
+            return launch_simt_kern<STAG_KDE_KERNEL_LOGISTIC>(h, grid, s, m, negc, tps, splits, count);
+        default:
+            return launch_simt_kern<STAG_KDE_KERNEL_GAUSSIAN>(h, grid, s, m, negc, tps, splits, count);
+    }
+}
+
 // Number of point-set splits: enough blocks for several waves of 2 blocks per SM.
 static int64_t choose_tiles_per_split(const stag_kde *h, int64_t q_tiles) {
     const int64_t target_blocks = (int64_t)h->sm_count * 2 * 6;
@@ -425,16 +457,10 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
     rc = ensure_partials(h, splits * m);
     if (rc) return rc;
     if (q_tiles > 0x7fffffff || splits > 65535) return fail(STAG_KDE_EINVAL, "query batch too large");
-    const float negc = (float)(-h->a * 1.4426950408889634);  // -a log2(e)
     dim3 grid((unsigned)q_tiles, (unsigned)splits);
     count_launch();
     prof_start(h, s);
-    if (h->d_pad <= kSimtKC)
-        kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
-                                                      tps, splits, h->part.sum, h->part.shift, nullptr);
-    else
-        kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc,
-                                                       tps, splits, h->part.sum, h->part.shift, nullptr);
+    launch_simt(h, grid, s, m, tps, splits, nullptr);
     prof_stop(h, s, (double)m * (double)h->n);
     STAG_CUDA_TRY(cudaGetLastError());
     return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
@@ -468,14 +494,7 @@ int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, con
     count_launch(3);
     gather_rows_tiles_kernel<<<grid_for(q_tiles * h->d_pad * kSimtTile, 256), 256, 0, s>>>(dQ, h->d, h->d_pad, idx,
                                                                                            count, m, h->qt);
-    const float negc = (float)(-h->a * 1.4426950408889634);
-    const unsigned grid = (unsigned)(h->sm_count * 2);
-    if (h->d_pad <= kSimtKC)
-        kde_simt_f32_kernel<true><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps, splits,
-                                                      h->part.sum, h->part.shift, count);
-    else
-        kde_simt_f32_kernel<false><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
-                                                       splits, h->part.sum, h->part.shift, count);
+    launch_simt(h, dim3((unsigned)(h->sm_count * 2)), s, m, tps, splits, count);
     combine_scatter_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
         h->part.sum, h->part.shift, m, (int)splits, idx, count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
     STAG_CUDA_TRY(cudaGetLastError());
@@ -520,7 +539,8 @@ int simt_query_f64(stag_kde *h, const double *dQ, int64_t m, double *dOut, cudaS
     if (smem > 48 * 1024) return fail(STAG_KDE_EUNSUPPORTED, "FP64 form: d too large");
     count_launch();
     prof_start(h, s);
-    kde_simt_f64_kernel<<<(unsigned)ceil_div(m, 128), 128, smem, s>>>(h->x64, h->n, dQ, m, h->d, h->a, dOut);
+    kde_simt_f64_kernel<<<(unsigned)ceil_div(m, 128), 128, smem, s>>>(h->x64, h->n, dQ, m, h->d, h->a, h->kernel,
+                                                                       dOut);
     prof_stop(h, s, (double)m * (double)h->n);
     STAG_CUDA_TRY(cudaGetLastError());
     if (h->normalise) {

@@ -18,20 +18,26 @@
 namespace stagkde {
 
 static thread_local std::string g_last_error;
+static thread_local int g_last_code = STAG_KDE_OK;
 static std::atomic<uint64_t> g_launches{0};
 
 void count_launch(int k) { g_launches.fetch_add((uint64_t)k, std::memory_order_relaxed); }
 void uncount_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
-void set_error(const std::string &msg) { g_last_error = msg; }
+void set_error(const std::string &msg) {
+    g_last_error = msg;
+    g_last_code = STAG_KDE_EINVAL;
+}
 
 int fail(int code, const std::string &msg) {
     g_last_error = msg;
+    g_last_code = code;
     return code;
 }
 
 int cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    g_last_code = STAG_KDE_ECUDA;
     return STAG_KDE_ECUDA;
 }
 
@@ -109,6 +115,8 @@ void free_handle(stag_kde *h) {
         cudaFree(h->x64);
     }
     cudaFree(h->q_dev);
+    cudaFree(h->xrow);
+    cudaFree(h->sub_dev);
     cudaFree(h->qt);
     cudaFree(h->out_dev);
     cudaFree(h->part.sum);
@@ -134,6 +142,7 @@ stag_kde *make_view(stag_kde *base) {
     v->dtype = base->dtype;
     v->form = base->form;
     v->normalise = base->normalise;
+    v->kernel = base->kernel;
     v->tc_check = base->tc_check;
     v->tune_eg = base->tune_eg;
     v->tune_tiles_per_unit = base->tune_tiles_per_unit;
@@ -162,7 +171,10 @@ void free_view(stag_kde *view) { free_handle(view); }
 
 namespace {
 
-int resolve_form(int requested, int dtype, int64_t d, int *form) {
+int resolve_form(int requested, int dtype, int64_t d, int kernel, int *form) {
+    if (kernel != STAG_KDE_KERNEL_GAUSSIAN && kernel != STAG_KDE_KERNEL_EXPONENTIAL &&
+        kernel != STAG_KDE_KERNEL_LOGISTIC)
+        return fail(STAG_KDE_EINVAL, "unknown kernel function");
     if (dtype == STAG_KDE_F64) {
         if (requested != STAG_KDE_FORM_AUTO && requested != STAG_KDE_FORM_SIMT_F64)
             return fail(STAG_KDE_EUNSUPPORTED, "FP64 data supports only the FP64 form");
@@ -171,12 +183,14 @@ int resolve_form(int requested, int dtype, int64_t d, int *form) {
     }
     switch (requested) {
         case STAG_KDE_FORM_AUTO:
-            *form = tc_supported(d) ? STAG_KDE_FORM_TC : STAG_KDE_FORM_SIMT_F32;
+            *form = kernel == STAG_KDE_KERNEL_GAUSSIAN && tc_supported(d) ? STAG_KDE_FORM_TC : STAG_KDE_FORM_SIMT_F32;
             return 0;
         case STAG_KDE_FORM_SIMT_F32:
             *form = requested;
             return 0;
         case STAG_KDE_FORM_TC:
+            if (kernel != STAG_KDE_KERNEL_GAUSSIAN)
+                return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form serves only the Gaussian kernel");
             if (!tc_supported(d)) return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form does not support this d");
             *form = requested;
             return 0;
@@ -239,7 +253,9 @@ stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, d
                                           : host_values_ok((const double *)X, n * d);
     if (!ok) return (set_error("X has a non-finite value or |x| > 1e15"), nullptr);
     int form = 0;
-    if (resolve_form(o.form, dtype, d, &form)) return nullptr;
+    for (int r : o.reserved)
+        if (r != 0) return (set_error("stag_kde_opts.reserved must be zero"), nullptr);
+    if (resolve_form(o.form, dtype, d, o.kernel, &form)) return nullptr;
 
     stag_kde *h = new (std::nothrow) stag_kde();
     if (!h) return (set_error("out of host memory"), nullptr);
@@ -259,6 +275,7 @@ stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, d
     h->dtype = dtype;
     h->form = form;
     h->normalise = o.normalise ? 1 : 0;
+    h->kernel = o.kernel;
     h->tc_check = o.tc_no_check == 0;
     auto bail = [&](const char *what, cudaError_t e) -> stag_kde_t * {
         if (e != cudaSuccess) cuda_fail(e, what);
@@ -368,6 +385,63 @@ int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, v
     return run_query(h, dQ, m, dOut, (cudaStream_t)stream, nullptr);
 }
 
+int stag_kde_query_subset_dev(stag_kde_t *h, const float *dQ, int64_t m, const int64_t *dOff, const int64_t *dIdx,
+                              const float *dW, double *dOut, void *stream) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (m < 0) return fail(STAG_KDE_EINVAL, "m < 0");
+    if (m == 0) return 0;
+    if (!dQ || !dOff || !dIdx || !dOut) return fail(STAG_KDE_EINVAL, "dQ, dOff, dIdx or dOut is NULL");
+    if (h->dtype != STAG_KDE_F32) return fail(STAG_KDE_EUNSUPPORTED, "subset sums: FP32 handles only");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
+    return subset_query(h, dQ, m, dOff, dIdx, dW, dOut, (cudaStream_t)stream, 0.0);
+}
+
+int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_t *off, const int64_t *idx,
+                          const float *W, double *out) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (m < 0) return fail(STAG_KDE_EINVAL, "m < 0");
+    if (m == 0) return 0;
+    if (!Q || !off || !out) return fail(STAG_KDE_EINVAL, "Q, off or out is NULL");
+    if (h->dtype != STAG_KDE_F32) return fail(STAG_KDE_EUNSUPPORTED, "subset sums: FP32 handles only");
+    if (off[0] != 0) return fail(STAG_KDE_EINVAL, "off[0] must be 0");
+    for (int64_t j = 0; j < m; ++j)
+        if (off[j + 1] < off[j]) return fail(STAG_KDE_EINVAL, "offsets must be non-decreasing");
+    const int64_t nnz = off[m];
+    if (nnz > 0 && !idx) return fail(STAG_KDE_EINVAL, "idx is NULL");
+    for (int64_t p = 0; p < nnz; ++p)
+        if (idx[p] < 0 || idx[p] >= h->n) return fail(STAG_KDE_EINVAL, "an index is outside [0, n)");
+    if (W)
+        for (int64_t p = 0; p < nnz; ++p)
+            if (!(W[p] >= 0.f) || !isfinite(W[p])) return fail(STAG_KDE_EINVAL, "weights must be finite and >= 0");
+    if (!host_values_ok(Q, m * h->d)) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
+    DeviceGuard g(h->device);
+    if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
+    // one device buffer: offsets | indices | weights | queries (16-byte aligned parts)
+    const int64_t b_off = round_up((m + 1) * 8, 16), b_idx = round_up(std::max<int64_t>(nnz, 1) * 8, 16);
+    const int64_t b_w = round_up(std::max<int64_t>(nnz, 1) * 4, 16), b_q = round_up(m * h->d * 4, 16);
+    int rc = ensure_bytes(&h->sub_dev, &h->sub_dev_cap, b_off + b_idx + b_w + b_q);
+    if (rc) return rc;
+    rc = ensure_bytes((void **)&h->out_dev, &h->out_cap, m * 8);
+    if (rc) return rc;
+    char *base = (char *)h->sub_dev;
+    int64_t *dOff = (int64_t *)base, *dIdx = (int64_t *)(base + b_off);
+    float *dW = (float *)(base + b_off + b_idx), *dQ = (float *)(base + b_off + b_idx + b_w);
+    cudaStream_t s = h->stream;
+    STAG_CUDA_TRY(cudaMemcpyAsync(dOff, off, (m + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dIdx, idx, nnz * 8, cudaMemcpyHostToDevice, s));
+    if (W && nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dW, W, nnz * 4, cudaMemcpyHostToDevice, s));
+    STAG_CUDA_TRY(cudaMemcpyAsync(dQ, Q, m * h->d * 4, cudaMemcpyHostToDevice, s));
+    rc = subset_query(h, dQ, m, dOff, dIdx, W ? dW : nullptr, h->out_dev, s, (double)nnz);
+    if (rc) {
+        cudaStreamSynchronize(s);
+        return rc;
+    }
+    STAG_CUDA_TRY(cudaMemcpyAsync(out, h->out_dev, m * 8, cudaMemcpyDeviceToHost, s));
+    STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
 int stag_kde_degrees(stag_kde_t *h, int exclude_self, double *dOut, void *stream) {
     if (!h || !dOut) return fail(STAG_KDE_EINVAL, "handle or dOut is NULL");
     if (h->dtype != STAG_KDE_F32) return fail(STAG_KDE_EUNSUPPORTED, "degrees: FP32 handles only");
@@ -435,6 +509,8 @@ int stag_kde_profile_end(stag_kde_t *h, double *ms, int64_t *launches, double *p
 }
 
 const char *stag_kde_last_error(void) { return g_last_error.c_str(); }
+
+int stag_kde_last_error_code(void) { return g_last_code; }
 
 const char *stag_kde_version(void) { return "stag-kde-gb300 0.1 (sm_103a)"; }
 

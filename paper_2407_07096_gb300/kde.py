@@ -5,6 +5,8 @@ App. A): it is built from a data matrix and the bandwidth a, and ``query`` retur
 kernel density of every row of a query matrix,
     K(q) = sum_i exp(-a ||q - x_i||^2)            (normalise=False, the default)
     K(q) = (1/n) sum_i exp(-a ||q - x_i||^2)      (normalise=True, Sec. 3's definition)
+``kernel`` selects Sec. 3's other kernel functions of r = ||q - x_i||: "exponential",
+exp(-a r), or "logistic", 4 / (2 + exp(a r) + exp(-a r)) (plain FP32 and FP64 forms).
 All arithmetic happens in the CUDA kernels behind ``libstagkde.so``.
 """
 from __future__ import annotations
@@ -27,7 +29,7 @@ class ExactGaussianKDE:
     """Exact Gaussian kernel density over a point set resident on one GPU."""
 
     def __init__(self, X, a: float, form: str = "auto", normalise: bool = False,
-                 device: int | None = None, dtype=None, tc_check: bool = True):
+                 device: int | None = None, dtype=None, tc_check: bool = True, kernel: str = "gaussian"):
         lib = L.load()
         try:
             import torch
@@ -47,13 +49,17 @@ class ExactGaussianKDE:
         opts.normalise = 1 if normalise else 0
         opts.device = -1 if device is None else int(device)
         opts.tc_no_check = 0 if tc_check else 1
+        if kernel not in L.KERNELS:
+            raise ValueError(f"unknown kernel {kernel!r}; one of {sorted(L.KERNELS)}")
+        opts.kernel = L.KERNELS[kernel]
         h = lib.stag_kde_create_ex(Xh.ctypes.data, self._dt, Xh.shape[0], Xh.shape[1], float(a),
                                    ctypes.byref(opts))
         if not h:
-            raise L.StagKdeError(L.EINVAL, L.last_error())
+            raise L.StagKdeError(lib.stag_kde_last_error_code() or L.EINVAL, L.last_error())
         self._h = ctypes.c_void_p(h)
         self._lib = lib
         self.n, self.d, self.a = int(Xh.shape[0]), int(Xh.shape[1]), float(a)
+        self.kernel = kernel
 
     @property
     def form(self) -> str:
@@ -105,6 +111,47 @@ class ExactGaussianKDE:
         ms, n, pairs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double()
         L.check(self._lib.stag_kde_profile_end(self._h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(pairs)))
         return ms.value, n.value, pairs.value
+
+    def query_subset(self, Q, offsets, idx, W=None) -> np.ndarray:
+        """Weighted subset sums (Sec. 3.1): out[j] = sum over query j's list entries
+        p = offsets[j] .. offsets[j+1]-1 of W[p] k(||q_j - x_{idx[p]}||) (W None: all 1),
+        host arrays, synchronous."""
+        Qh = _as_host(Q, np.float32)
+        if Qh.shape[1] != self.d:
+            raise ValueError(f"Q has d={Qh.shape[1]}, the data has d={self.d}")
+        m = Qh.shape[0]
+        off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+        ix = np.ascontiguousarray(np.asarray(idx, dtype=np.int64))
+        if off.shape != (m + 1,):
+            raise ValueError("offsets must have m + 1 entries")
+        w = None if W is None else np.ascontiguousarray(np.asarray(W, dtype=np.float32))
+        out = np.empty(m, dtype=np.float64)
+        L.check(self._lib.stag_kde_query_subset(self._h, Qh.ctypes.data, m, off.ctypes.data,
+                                                ix.ctypes.data if ix.size else None,
+                                                None if w is None else w.ctypes.data, out.ctypes.data))
+        return out
+
+    def query_subset_dev(self, Q, offsets, idx, W=None, out=None, stream=None):
+        """Device variant of query_subset on CUDA tensors (Q float32 m x d, offsets and
+        idx int64, W float32 or None); queued on ``stream``, returns ``out``."""
+        import torch
+        for t in (Q, offsets, idx) + (() if W is None else (W,)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+                raise ValueError("Q, offsets, idx and W must be contiguous CUDA tensors")
+        if Q.dtype != torch.float32 or offsets.dtype != torch.int64 or idx.dtype != torch.int64:
+            raise ValueError("Q float32, offsets and idx int64")
+        if W is not None and W.dtype != torch.float32:
+            raise ValueError("W must be float32")
+        m = Q.shape[0]
+        if Q.dim() != 2 or Q.shape[1] != self.d or offsets.numel() != m + 1:
+            raise ValueError("Q must be m x d and offsets m + 1 long")
+        if out is None:
+            out = torch.empty(m, dtype=torch.float64, device=Q.device)
+        s = (stream or torch.cuda.current_stream()).cuda_stream
+        L.check(self._lib.stag_kde_query_subset_dev(self._h, Q.data_ptr(), m, offsets.data_ptr(),
+                                                    idx.data_ptr() if idx.numel() else offsets.data_ptr(),
+                                                    None if W is None else W.data_ptr(), out.data_ptr(), s))
+        return out
 
     def degrees(self, exclude_self: bool = False, stream=None):
         """Similarity-graph degrees of the handle's own points (Sec. 4.1), a CUDA tensor."""
