@@ -5,7 +5,8 @@ CPU-baseline leg may use it; the library's product path never imports it, and it
 imports nothing from the library. It implements the paper's definition of the
 kernel density (Sec. 3) with the Gaussian kernel (Sec. 3) as a plain double loop, the
 same for Sec. 3's exponential and logistic kernels, and the weighted subset sums of the
-sampling estimators (Sec. 3.1).
+sampling estimators (Sec. 3.1); and the Euclidean LSH of Sec. 2 (hash values and
+near-neighbour candidate lists, lsh_oracle.c).
 """
 from .kde import (build, kde, kde_weighted, kde_self, kde_log, kde_kernel, kde_subset,  # noqa: F401
-                  KERNELS, rel_err, avg_rel_err)
+                  KERNELS, lsh_hash, lsh_candidates, rel_err, avg_rel_err)

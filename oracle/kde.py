@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "kde_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _SO = os.path.join(_OUT_DIR, "libkdeoracle.so")
+_SRC_LSH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lsh_oracle.c")
 _lock = threading.Lock()
 _lib = None
 
@@ -27,10 +28,11 @@ _D = ctypes.POINTER(ctypes.c_double)
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (-O2, no fast-math: IEEE double, libm exp)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+    srcs = [_SRC, _SRC_LSH]
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(p) for p in srcs):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.run(["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fPIC", "-shared",
-                        "-o", tmp, _SRC, "-lm", "-lpthread"], check=True)
+                        "-o", tmp, *srcs, "-lm", "-lpthread"], check=True)
         os.replace(tmp, _SO)
     return _SO
 
@@ -51,6 +53,11 @@ def _load():
             for f in (lib.oracle_kde, lib.oracle_kde_weighted, lib.oracle_kde_self, lib.oracle_kde_log,
                       lib.oracle_kde_kernel, lib.oracle_kde_subset):
                 f.restype = c_int
+            F, I32 = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)
+            lib.oracle_lsh_hash.argtypes = [F, i64, i64, i64, F, F, I32]
+            lib.oracle_lsh_hash.restype = c_int
+            lib.oracle_lsh_candidates.argtypes = [I32, i64, I32, i64, c_int, c_int, _I, _I, i64]
+            lib.oracle_lsh_candidates.restype = i64
             _lib = lib
     return _lib
 
@@ -136,6 +143,43 @@ def kde_subset(X, Q, a: float, offsets, idx, W=None, kernel: str = "gaussian",
     if rc:
         raise ValueError(f"oracle_kde_subset failed ({rc})")
     return out
+
+
+def lsh_hash(X, A, B) -> np.ndarray:
+    """E2LSH hash values floor((<x, a_f> + b_f) / 4) of the rows of X under the functions
+    (rows of A, offsets B), taken in FP32 (fused multiply-adds in coordinate order), as an
+    n x nf int32 array (Sec. 2)."""
+    X = np.ascontiguousarray(np.asarray(X, dtype=np.float32))
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float32))
+    B = np.ascontiguousarray(np.asarray(B, dtype=np.float32)).reshape(-1)
+    if X.ndim != 2 or A.ndim != 2 or A.shape[1] != X.shape[1] or B.shape[0] != A.shape[0]:
+        raise ValueError("X (n x d), A (nf x d), B (nf)")
+    H = np.empty((X.shape[0], A.shape[0]), dtype=np.int32)
+    F, I32 = ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)
+    rc = _load().oracle_lsh_hash(X.ctypes.data_as(F), X.shape[0], X.shape[1], A.shape[0], A.ctypes.data_as(F),
+                                 B.ctypes.data_as(F), H.ctypes.data_as(I32))
+    if rc:
+        raise ValueError("oracle_lsh_hash failed")
+    return H
+
+
+def lsh_candidates(HX, HQ, K: int, L: int):
+    """Near-neighbour lists (Sec. 2): for each query row of HQ, the distinct indices i, in
+    increasing order, whose K hash values equal the query's in at least one of the L
+    tables. Returns (offsets[m + 1], idx)."""
+    HX = np.ascontiguousarray(HX, dtype=np.int32)
+    HQ = np.ascontiguousarray(HQ, dtype=np.int32)
+    if HX.shape[1] != K * L or HQ.shape[1] != K * L:
+        raise ValueError("hash arrays must have K * L columns")
+    lib = _load()
+    I32, I = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    off = np.empty(HQ.shape[0] + 1, dtype=np.int64)
+    total = lib.oracle_lsh_candidates(HX.ctypes.data_as(I32), HX.shape[0], HQ.ctypes.data_as(I32), HQ.shape[0],
+                                      K, L, off.ctypes.data_as(I), None, 0)
+    idx = np.empty(max(total, 1), dtype=np.int64)
+    lib.oracle_lsh_candidates(HX.ctypes.data_as(I32), HX.shape[0], HQ.ctypes.data_as(I32), HQ.shape[0],
+                              K, L, off.ctypes.data_as(I), idx.ctypes.data_as(I), total)
+    return off, idx[:total]
 
 
 def kde_self(X, a: float, threads: int | None = None) -> np.ndarray:
