@@ -154,6 +154,54 @@ int stag_kde_query_subset_dev(stag_kde_t *h, const float *dQ, int64_t m, const i
                               const float *dW, double *dOut, void *stream);
 
 /*
+ * ------------------------------------------------------------------ Euclidean LSH
+ * E2LSH tables (Sec. 2), the candidate generator of the LSH-based estimators (Sec. 3.1):
+ * L tables, each keyed by K hash functions h_{a,b}(x) = floor((<x, a> + b) / 4). The
+ * caller supplies the L*K functions: A (L*K x d, row-major; row l*K + k is function k of
+ * table l; drawn from N(0, I)) and B (L*K offsets, drawn from U(0, 4)); the library
+ * draws no random numbers. Each hash value is decided in FP32 with a fixed order
+ * (s = 0; s = fma(x_k, a_k, s) for k = 0..d-1; floor((s + b) * 0.25), saturated to int32),
+ * so values are reproducible bit for bit. A point and a query share table l's bucket when
+ * their K values of that table agree (buckets are keyed by a 58-bit mix of the K values;
+ * two different K-tuples collide with probability ~2^-58 per pair).
+ */
+typedef struct stag_lsh stag_lsh_t; /* opaque handle */
+
+/* Builds the L tables over X (n x d FP32, host; copied, not retained) on `device`
+ * (-1 = current). Requires n < 2^32, d <= 384, K >= 1, 1 <= L <= 63, K*L <= 4096, finite
+ * inputs. Returns NULL on error (stag_kde_last_error / stag_kde_last_error_code). */
+stag_lsh_t *stag_lsh_create(const float *X, int64_t n, int64_t d, int K, int L, const float *A, const float *B,
+                            int device);
+
+/* Hash values of the rows of dQ (m x d FP32, device) under all L*K functions into dH
+ * (m x L*K int32, device, row-major), queued on `stream`. */
+int stag_lsh_hash_dev(stag_lsh_t *h, const float *dQ, int64_t m, int32_t *dH, void *stream);
+
+/*
+ * Near-neighbour candidates: for every query, the distinct points that share its bucket
+ * in at least one table, in increasing index order, as CSR lists (off has m + 1 entries).
+ * Host variant: Q (m x d FP32, host) is validated (finite); off always receives the
+ * offsets and *total the number of candidates; idx receives the indices only when it is
+ * not NULL and cap >= *total (otherwise call again with a large enough buffer).
+ * Device variant: dQ, dOff (m + 1 int64) and dIdx (cap int64, or NULL) are device
+ * buffers; dOff and *total are always written, the indices only when cap >= *total. The
+ * handle keeps the last device query's lists: stag_lsh_fetch_dev copies them into a
+ * large enough buffer without recomputing. Both variants synchronise the stream (the
+ * list sizes decide allocations). The lists feed stag_kde_query_subset[_dev] directly.
+ */
+int stag_lsh_query(stag_lsh_t *h, const float *Q, int64_t m, int64_t *off, int64_t *idx, int64_t cap,
+                   int64_t *total);
+int stag_lsh_query_dev(stag_lsh_t *h, const float *dQ, int64_t m, int64_t *dOff, int64_t *dIdx, int64_t cap,
+                       int64_t *total, void *stream);
+int stag_lsh_fetch_dev(stag_lsh_t *h, int64_t *dIdx, int64_t cap, void *stream);
+
+/* Sizes of the handle (any pointer may be NULL). */
+int stag_lsh_info(const stag_lsh_t *h, int64_t *n, int64_t *d, int *K, int *L);
+
+/* Releases the tables. NULL-safe. */
+void stag_lsh_destroy(stag_lsh_t *h);
+
+/*
  * Batched evaluation: instance i evaluates the device query matrix dQs[i] (ms[i] rows,
  * the handle's element type and d) against handle hs[i] into dOuts[i] (ms[i] doubles).
  * The handles must be distinct and live on one device; ms[i] may differ, and so may the

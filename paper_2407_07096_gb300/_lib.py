@@ -51,6 +51,13 @@ SIGNATURES = [
     ("stag_kde_query_dev", _INT, [_VP, _VP, _I64, _VP, _VP]),
     ("stag_kde_query_subset", _INT, [_VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     ("stag_kde_query_subset_dev", _INT, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
+    ("stag_lsh_create", _VP, [_VP, _I64, _I64, _INT, _INT, _VP, _VP, _INT]),
+    ("stag_lsh_hash_dev", _INT, [_VP, _VP, _I64, _VP, _VP]),
+    ("stag_lsh_query", _INT, [_VP, _VP, _I64, _VP, _VP, _I64, _VP]),
+    ("stag_lsh_query_dev", _INT, [_VP, _VP, _I64, _VP, _VP, _I64, _VP, _VP]),
+    ("stag_lsh_fetch_dev", _INT, [_VP, _VP, _I64, _VP]),
+    ("stag_lsh_info", _INT, [_VP, _VP, _VP, _VP, _VP]),
+    ("stag_lsh_destroy", None, [_VP]),
     ("stag_kde_reserve", _INT, [_VP, _I64]),
     ("stag_kde_query_batch", _INT, [ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(_I64),
                                     ctypes.POINTER(_VP), _I64, _VP]),

@@ -211,9 +211,9 @@ int grid_of(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_div
 }  // namespace
 
 // Stable sort of (keys, vals) by key bits [0, bits), ping-ponging with the tmp buffers;
-// the result ends in (keys, vals).
-static int radix_sort(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t *hist, int64_t n,
-                      int bits, cudaStream_t s) {
+// the result ends in (keys, vals). hist needs 256 * ceil(n / 4096) entries.
+int radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t *hist, int64_t n,
+                     int bits, cudaStream_t s) {
     const int nblocks = (int)ceil_div(n, kRsChunk);
     uint64_t *ka = keys, *kb = ktmp;
     uint32_t *va = vals, *vb = vtmp;
@@ -278,7 +278,7 @@ int kd_reorder(const float *dX, int64_t n, int64_t d, int BN, float *dXs, cudaSt
         kd_keys_kernel<<<grid_of(n, 256), 256, 0, s>>>(dX, n, d, BN, T, level, perm, dim, keys, vtmp);
         // sort (segment, coordinate) keys; the values are the point indices
         uint32_t *vals = vtmp;
-        rc = radix_sort(keys, vals, ktmp, perm, hist, n, 32 + level, s);
+        rc = radix_sort_pairs(keys, vals, ktmp, perm, hist, n, 32 + level, s);
         if (!rc) {
             // sorted point indices are now in `vtmp`; make them the current order
             std::swap(perm, vtmp);
