@@ -138,10 +138,15 @@ int launch_combine(const double *part_sum, const float *part_shift, int64_t m, i
 
 // kd_order.cu
 // Stable LSD radix sort of (64-bit key, 32-bit value) pairs by key bits [0, bits); the
-// result ends in (keys, vals); hist holds 256 * radix_sort_blocks(n) entries.
+// result ends in (keys, vals); hist holds radix_sort_hist_entries(n) entries (the digit
+// histogram, 256 per block of 4096 keys, and the totals of its scan chunks).
 int radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t *hist, int64_t n,
                      int bits, cudaStream_t s);
 inline int64_t radix_sort_blocks(int64_t n) { return ceil_div(n, 4096); }
+inline int64_t radix_sort_hist_entries(int64_t n) {
+    const int64_t e = 256 * radix_sort_blocks(n);
+    return e + ceil_div(e, 4096) + 1;
+}
 int kd_reorder(const float *dX, int64_t n, int64_t d, int BN, float *dXs, cudaStream_t s);
 
 // kde_tc.cu

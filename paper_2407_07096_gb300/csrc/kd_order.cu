@@ -62,6 +62,47 @@ __global__ void rs_hist_kernel(const uint64_t *__restrict__ keys, int64_t n, int
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
+// Exclusive scan of the histogram, in two levels: every block scans one chunk of
+// kScanChunk entries in place and writes the chunk's total to part[chunk]; one block then
+// scans the chunk totals (rs_scan_kernel), and the scatter adds part[entry / kScanChunk].
+constexpr int kScanThreads = 1024;
+constexpr int kScanChunk = 4 * kScanThreads;
+
+__global__ void __launch_bounds__(kScanThreads)
+rs_scan_chunks_kernel(uint32_t *__restrict__ a, int64_t count, uint32_t *__restrict__ part) {
+    __shared__ uint32_t wsum[32];
+    const int64_t i0 = (int64_t)blockIdx.x * kScanChunk + 4 * threadIdx.x;
+    uint32_t v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = i0 + e < count ? a[i0 + e] : 0u;
+    const uint32_t t0 = v[0], t1 = t0 + v[1], t2 = t1 + v[2], t3 = t2 + v[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = t3;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        wsum[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t excl = (warp ? wsum[warp - 1] : 0u) + inc - t3;
+    const uint32_t out[4] = {excl, excl + t0, excl + t1, excl + t2};
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+        if (i0 + e < count) a[i0 + e] = out[e];
+    if (threadIdx.x == kScanThreads - 1) part[blockIdx.x] = wsum[31];
+}
+
 // exclusive scan of `count` entries in place (single block of 1024 threads)
 __global__ void rs_scan_kernel(uint32_t *__restrict__ a, int64_t count) {
     __shared__ uint32_t s[1024];
@@ -90,11 +131,13 @@ __global__ void rs_scan_kernel(uint32_t *__restrict__ a, int64_t count) {
 // match masks and per-warp digit counts.
 __global__ void __launch_bounds__(kRsThreads)
 rs_scatter_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                  uint32_t *__restrict__ vout, int64_t n, int shift, int nblocks, const uint32_t *__restrict__ hist) {
+                  uint32_t *__restrict__ vout, int64_t n, int shift, int nblocks, const uint32_t *__restrict__ hist,
+                  const uint32_t *__restrict__ part) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t cnt[kRsThreads / 32][256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    base[threadIdx.x] = hist[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const int64_t hidx = (int64_t)threadIdx.x * nblocks + blockIdx.x;
+    base[threadIdx.x] = hist[hidx] + part[hidx / kScanChunk];
     for (int w = 0; w < kRsThreads / 32; ++w) cnt[w][threadIdx.x] = 0;
     __syncthreads();
     const int64_t b0 = (int64_t)blockIdx.x * kRsChunk;
@@ -211,18 +254,22 @@ int grid_of(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_div
 }  // namespace
 
 // Stable sort of (keys, vals) by key bits [0, bits), ping-ponging with the tmp buffers;
-// the result ends in (keys, vals). hist needs 256 * ceil(n / 4096) entries.
+// the result ends in (keys, vals). hist needs radix_sort_hist_entries(n) entries.
 int radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t *hist, int64_t n,
                      int bits, cudaStream_t s) {
     const int nblocks = (int)ceil_div(n, kRsChunk);
+    const int64_t entries = (int64_t)256 * nblocks;
+    const int64_t chunks = ceil_div(entries, kScanChunk);
+    uint32_t *part = hist + entries;  // chunk totals, scanned in place
     uint64_t *ka = keys, *kb = ktmp;
     uint32_t *va = vals, *vb = vtmp;
     int passes = 0;
     for (int shift = 0; shift < bits; shift += 8, ++passes) {
-        count_launch(3);
+        count_launch(4);
         rs_hist_kernel<<<nblocks, 256, 0, s>>>(ka, n, shift, nblocks, hist);
-        rs_scan_kernel<<<1, 1024, 0, s>>>(hist, (int64_t)256 * nblocks);
-        rs_scatter_kernel<<<nblocks, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, nblocks, hist);
+        rs_scan_chunks_kernel<<<(unsigned)chunks, kScanThreads, 0, s>>>(hist, entries, part);
+        rs_scan_kernel<<<1, 1024, 0, s>>>(part, chunks);
+        rs_scatter_kernel<<<nblocks, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, nblocks, hist, part);
         std::swap(ka, kb);
         std::swap(va, vb);
     }
@@ -260,7 +307,7 @@ int kd_reorder(const float *dX, int64_t n, int64_t d, int BN, float *dXs, cudaSt
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&perm, n * 4)) || (e = cudaMalloc(&vtmp, n * 4)) || (e = cudaMalloc(&keys, n * 8)) ||
         (e = cudaMalloc(&ktmp, n * 8)) || (e = cudaMalloc(&mn, max_seg * d * 4)) ||
-        (e = cudaMalloc(&mx, max_seg * d * 4)) || (e = cudaMalloc(&hist, (int64_t)256 * nblocks * 4)) ||
+        (e = cudaMalloc(&mx, max_seg * d * 4)) || (e = cudaMalloc(&hist, radix_sort_hist_entries(n) * 4)) ||
         (e = cudaMalloc(&dim, max_seg * sizeof(int)))) {
         cleanup();
         return cuda_fail(e, "cudaMalloc(k-d ordering)");

@@ -254,9 +254,8 @@ int lsh_run(stag_lsh *h, const float *dQ, int64_t m, int64_t *dOff, cudaStream_t
     STAG_CUDA_TRY(cudaMemcpyAsync(&R, raw_off + m, 8, cudaMemcpyDeviceToHost, s));
     STAG_CUDA_TRY(cudaStreamSynchronize(s));
     // raw keys + sort buffers: keys, ktmp (R u64 each), vals, vtmp (R u32 each), hist
-    const int64_t nb = radix_sort_blocks(std::max<int64_t>(R, 1));
     const int64_t b_k = round_up(std::max<int64_t>(R, 1) * 8, 256), b_v = round_up(std::max<int64_t>(R, 1) * 4, 256);
-    const int64_t b_h = round_up(256 * nb * 4, 256), b_u = round_up(m * 8, 256);
+    const int64_t b_h = round_up(radix_sort_hist_entries(std::max<int64_t>(R, 1)) * 4, 256), b_u = round_up(m * 8, 256);
     void *sort_buf = nullptr;
     STAG_CUDA_TRY(cudaMalloc(&sort_buf, 2 * b_k + 2 * b_v + b_h + b_u));
     char *sb = (char *)sort_buf;
@@ -379,11 +378,10 @@ stag_lsh_t *stag_lsh_create(const float *X, int64_t n, int64_t d, int K, int L, 
         cudaFree(sortb);
     };
     const int64_t nl = n * L;
-    const int64_t nb = radix_sort_blocks(nl);
     if ((e = cudaMalloc(&h->A, nf * d * 4)) != cudaSuccess || (e = cudaMalloc(&h->B, nf * 4)) != cudaSuccess ||
         (e = cudaMalloc(&h->keys, nl * 8)) != cudaSuccess || (e = cudaMalloc(&h->ids, nl * 4)) != cudaSuccess ||
         (e = cudaMalloc(&dX, n * d * 4)) != cudaSuccess || (e = cudaMalloc(&H, n * nf * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&sortb, nl * 12 + 256 * nb * 4)) != cudaSuccess) {
+        (e = cudaMalloc(&sortb, nl * 12 + radix_sort_hist_entries(nl) * 4)) != cudaSuccess) {
         cleanup();
         return (cuda_fail(e, "cudaMalloc (LSH tables)"), bail(0));
     }
