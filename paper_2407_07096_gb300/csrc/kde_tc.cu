@@ -53,6 +53,7 @@
 #include <type_traits>
 #include <mutex>
 
+#include "f32x2.cuh"
 #include "internal.h"
 #include "sm100_ptx.cuh"
 
@@ -915,6 +916,10 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
         }
         unorm[q0 + r] = real ? sqrtf(s) : 0.f;
     }
+    // the query as packed coordinate pairs: two differences and two FMAs per instruction
+    uint64_t qp[KP / 2];
+#pragma unroll
+    for (int k = 0; k < KP / 2; ++k) qp[k] = f2::pack(qv[2 * k], qv[2 * k + 1]);
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
     // upper bound on the exponent -c ||q - x||^2 over the tiles of this block: every x of
@@ -929,20 +934,23 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
         for (int e = threadIdx.x; e < gn; e += 128) srad[e] = tinfo[(g0 + e) * 4 + 1];
         __syncthreads();
         for (int j = 0; j < gn; ++j) {
-            float s0 = 0.f, s1 = 0.f;
+            uint64_t a01 = 0, a23 = 0;  // {0.f, 0.f}
 #pragma unroll
             for (int k = 0; k < KP; k += 4) {
                 const float4 cv = *reinterpret_cast<const float4 *>(&sc[j][k]);
-                const float d0 = qv[k] - cv.x, d1 = qv[k + 1] - cv.y, d2 = qv[k + 2] - cv.z, d3 = qv[k + 3] - cv.w;
-                s0 = fmaf(d0, d0, s0);
-                s1 = fmaf(d1, d1, s1);
-                s0 = fmaf(d2, d2, s0);
-                s1 = fmaf(d3, d3, s1);
+                const uint64_t d01 = f2::sub(qp[k / 2], f2::pack(cv.x, cv.y));
+                const uint64_t d23 = f2::sub(qp[k / 2 + 1], f2::pack(cv.z, cv.w));
+                a01 = f2::fma(d01, d01, a01);
+                a23 = f2::fma(d23, d23, a23);
             }
-            const float cr = c * (s0 + s1);
+            float s0, s1, s2, s3;
+            f2::unpack(a01, s0, s1);
+            f2::unpack(a23, s2, s3);
+            const float cr = c * ((s0 + s1) + (s2 + s3));
             R[(g0 + j) * m_pad + q0 + r] = real ? cr : 0.f;
-            // slack of a few ulps so that the bound holds for the FP32-computed exponents too
-            const float gap = fmaxf(0.f, sqrtf(cr) * (1.f - 1e-5f) - sqc * srad[j]);
+            // slack of 1e-5 relative (far above the approximate square root's ~2^-22 error
+            // and the FP32 rounding of the exponents) so that the bound holds
+            const float gap = fmaxf(0.f, ptx::sqrt_approx(cr) * (1.f - 1e-5f) - sqc * srad[j]);
             ubest = fmaxf(ubest, -gap * gap);
         }
     }
