@@ -185,7 +185,8 @@ int stag_lsh_hash_dev(stag_lsh_t *h, const float *dQ, int64_t m, int32_t *dH, vo
  * not NULL and cap >= *total (otherwise call again with a large enough buffer).
  * Device variant: dQ, dOff (m + 1 int64) and dIdx (cap int64, or NULL) are device
  * buffers; dOff and *total are always written, the indices only when cap >= *total. The
- * handle keeps the last device query's lists: stag_lsh_fetch_dev copies them into a
+ * handle keeps the last query's lists (either variant): stag_lsh_fetch (host memory,
+ * synchronous) and stag_lsh_fetch_dev (device memory, on `stream`) copy them into a
  * large enough buffer without recomputing. Both variants synchronise the stream (the
  * list sizes decide allocations). The lists feed stag_kde_query_subset[_dev] directly.
  */
@@ -193,6 +194,7 @@ int stag_lsh_query(stag_lsh_t *h, const float *Q, int64_t m, int64_t *off, int64
                    int64_t *total);
 int stag_lsh_query_dev(stag_lsh_t *h, const float *dQ, int64_t m, int64_t *dOff, int64_t *dIdx, int64_t cap,
                        int64_t *total, void *stream);
+int stag_lsh_fetch(stag_lsh_t *h, int64_t *idx, int64_t cap);
 int stag_lsh_fetch_dev(stag_lsh_t *h, int64_t *dIdx, int64_t cap, void *stream);
 
 /* Sizes of the handle (any pointer may be NULL). */

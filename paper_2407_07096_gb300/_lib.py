@@ -55,6 +55,7 @@ SIGNATURES = [
     ("stag_lsh_hash_dev", _INT, [_VP, _VP, _I64, _VP, _VP]),
     ("stag_lsh_query", _INT, [_VP, _VP, _I64, _VP, _VP, _I64, _VP]),
     ("stag_lsh_query_dev", _INT, [_VP, _VP, _I64, _VP, _VP, _I64, _VP, _VP]),
+    ("stag_lsh_fetch", _INT, [_VP, _VP, _I64]),
     ("stag_lsh_fetch_dev", _INT, [_VP, _VP, _I64, _VP]),
     ("stag_lsh_info", _INT, [_VP, _VP, _VP, _VP, _VP]),
     ("stag_lsh_destroy", None, [_VP]),

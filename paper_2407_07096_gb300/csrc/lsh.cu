@@ -466,10 +466,22 @@ int stag_lsh_query(stag_lsh_t *h, const float *Q, int64_t m, int64_t *off, int64
     h->last_total = 0;
     rc = lsh_run(h, dQ, m, dOff, s, total);
     if (rc) return rc;
+    h->last_total = *total;
     STAG_CUDA_TRY(cudaMemcpyAsync(off, dOff, (m + 1) * 8, cudaMemcpyDeviceToHost, s));
     if (idx && cap >= *total && *total > 0)
         STAG_CUDA_TRY(cudaMemcpyAsync(idx, h->cand, *total * 8, cudaMemcpyDeviceToHost, s));
     STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
+int stag_lsh_fetch(stag_lsh_t *h, int64_t *idx, int64_t cap) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (h->last_total == 0) return 0;
+    if (!idx || cap < h->last_total) return fail(STAG_KDE_EINVAL, "idx is NULL or cap is below the list size");
+    Guard g(h->device);
+    if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
+    STAG_CUDA_TRY(cudaMemcpyAsync(idx, h->cand, h->last_total * 8, cudaMemcpyDeviceToHost, h->stream));
+    STAG_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return 0;
 }
 

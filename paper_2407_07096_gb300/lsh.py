@@ -73,9 +73,8 @@ class E2LSH:
         L.check(self._lib.stag_lsh_query(self._h, Qh.ctypes.data, m, off.ctypes.data, None, 0,
                                          ctypes.byref(total)))
         idx = np.empty(max(total.value, 1), dtype=np.int64)
-        if total.value:
-            L.check(self._lib.stag_lsh_query(self._h, Qh.ctypes.data, m, off.ctypes.data, idx.ctypes.data,
-                                             total.value, ctypes.byref(total)))
+        if total.value:  # the lists the call kept, without recomputing them
+            L.check(self._lib.stag_lsh_fetch(self._h, idx.ctypes.data, idx.size))
         return off, idx[:total.value]
 
     def query_dev(self, Q, stream=None):
