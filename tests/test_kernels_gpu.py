@@ -25,10 +25,12 @@ def _kde_cls():
 
 def _kappa(X, Q, a, kernel):
     X64, Q64 = X.astype(np.float64), Q.astype(np.float64)
+    x2 = (X64 ** 2).sum(1)
     out = np.empty(len(Q64))
     for j0 in range(0, len(Q64), 64):
         q = Q64[j0:j0 + 64]
-        d2 = np.maximum(((q[:, None, :] - X64[None, :, :]) ** 2).sum(-1), 0.0)
+        # (only the tolerance depends on kappa: the expanded form is accurate enough here)
+        d2 = np.maximum((q ** 2).sum(1)[:, None] + x2[None, :] - 2.0 * q @ X64.T, 0.0)
         x = a * np.sqrt(d2)
         if kernel == "exponential":
             w, g = np.exp(-(x - x.min(1, keepdims=True))), x
@@ -129,3 +131,19 @@ def test_degrees_and_batch(kernel):
         solo = kde.query(q.cpu().numpy())
         assert np.array_equal(o.cpu().numpy(), solo)
         kde.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kernel", ["exponential", "logistic"])
+def test_kernels_workload_size_sampled(kernel):
+    # the benchmark's kernel-function workload in full (n = m = 100000, d = 16, a = 0.3),
+    # 256 sampled queries checked one by one against the oracle
+    K = _kde_cls()
+    X, Q = G.workload_single_d16(0)
+    a = 0.3
+    with K(X, a, form="simt_f32", kernel=kernel) as kde:
+        got = kde.query(Q)
+    rows = np.random.default_rng(6).choice(len(Q), 256, replace=False)
+    want = oracle.kde_kernel(X, Q[rows], a, kernel)
+    kap = _kappa(X, Q[rows], a, kernel)
+    assert np.all(oracle.rel_err(got[rows], want) <= tol_f32(kap, 16))
