@@ -129,6 +129,9 @@ int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStre
 // kde_subset.cu: weighted subset sums over per-query (index, weight) lists. `entries`
 // (the list entries, if known on the host) only feeds the profiling counters.
 int subset_prepare(stag_kde *h, cudaStream_t s);
+// Sets bit 0 of *dflag if an index lies outside [0, n), bit 1 if a weight is negative
+// or not finite.
+int subset_check_entries(const int64_t *dIdx, const float *dW, int64_t nnz, int64_t n, int *dflag, cudaStream_t s);
 int subset_query(stag_kde *h, const float *dQ, int64_t m, const int64_t *dOff, const int64_t *dIdx, const float *dW,
                  double *dOut, cudaStream_t s, double entries);
 

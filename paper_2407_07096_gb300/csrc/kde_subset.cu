@@ -124,7 +124,33 @@ void launch_kern(const stag_kde *h, const float *dQ, int64_t m, const int64_t *d
                                                                               dIdx, dW, negc, scale, dOut);
 }
 
+// Flags (bit 0) an index outside [0, n) and (bit 1) a weight that is negative or not
+// finite, over the nnz list entries.
+__global__ void subset_check_kernel(const int64_t *__restrict__ idx, const float *__restrict__ W, int64_t nnz,
+                                    int64_t n, int *flag) {
+    int bad = 0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx[p];
+        if (i < 0 || i >= n) bad |= 1;
+        if (W) {
+            const float w = W[p];
+            if (!(w >= 0.f) || !isfinite(w)) bad |= 2;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    if (bad && (threadIdx.x & 31) == 0) atomicOr(flag, bad);
+}
+
 }  // namespace
+
+int subset_check_entries(const int64_t *dIdx, const float *dW, int64_t nnz, int64_t n, int *dflag, cudaStream_t s) {
+    if (nnz <= 0) return 0;
+    count_launch();
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nnz, 256), 152 * 16));
+    subset_check_kernel<<<grid, 256, 0, s>>>(dIdx, dW, nnz, n, dflag);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
 
 int subset_prepare(stag_kde *h, cudaStream_t s) {
     if (h->xrow) return 0;

@@ -41,6 +41,8 @@ struct stag_lsh {
     void *host_q = nullptr;  // host API: device copies of Q and the offsets
     int64_t host_q_cap = 0;
     int64_t last_total = 0;  // size of the kept candidate lists (device query)
+    void *sort_buf = nullptr;  // raw candidate keys and radix-sort buffers (grown on demand)
+    int64_t sort_cap = 0;
 };
 
 namespace stagkde {
@@ -256,9 +258,9 @@ int lsh_run(stag_lsh *h, const float *dQ, int64_t m, int64_t *dOff, cudaStream_t
     // raw keys + sort buffers: keys, ktmp (R u64 each), vals, vtmp (R u32 each), hist
     const int64_t b_k = round_up(std::max<int64_t>(R, 1) * 8, 256), b_v = round_up(std::max<int64_t>(R, 1) * 4, 256);
     const int64_t b_h = round_up(radix_sort_hist_entries(std::max<int64_t>(R, 1)) * 4, 256), b_u = round_up(m * 8, 256);
-    void *sort_buf = nullptr;
-    STAG_CUDA_TRY(cudaMalloc(&sort_buf, 2 * b_k + 2 * b_v + b_h + b_u));
-    char *sb = (char *)sort_buf;
+    int rcs = grow(&h->sort_buf, &h->sort_cap, 2 * b_k + 2 * b_v + b_h + b_u);
+    if (rcs) return rcs;
+    char *sb = (char *)h->sort_buf;
     uint64_t *raw = (uint64_t *)sb, *ktmp = (uint64_t *)(sb + b_k);
     uint32_t *vals = (uint32_t *)(sb + 2 * b_k), *vtmp = (uint32_t *)(sb + 2 * b_k + b_v);
     uint32_t *hist = (uint32_t *)(sb + 2 * b_k + 2 * b_v);
@@ -293,7 +295,6 @@ int lsh_run(stag_lsh *h, const float *dQ, int64_t m, int64_t *dOff, cudaStream_t
         }
     }
     cudaStreamSynchronize(s);
-    cudaFree(sort_buf);
     return rc;
 }
 
@@ -322,6 +323,7 @@ void free_lsh(stag_lsh *h) {
     cudaFree(h->ids);
     cudaFree(h->scratch);
     cudaFree(h->cand);
+    cudaFree(h->sort_buf);
     cudaFree(h->host_q);
     if (h->stream) cudaStreamDestroy(h->stream);
     delete h;

@@ -409,12 +409,9 @@ int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_
         if (off[j + 1] < off[j]) return fail(STAG_KDE_EINVAL, "offsets must be non-decreasing");
     const int64_t nnz = off[m];
     if (nnz > 0 && !idx) return fail(STAG_KDE_EINVAL, "idx is NULL");
-    for (int64_t p = 0; p < nnz; ++p)
-        if (idx[p] < 0 || idx[p] >= h->n) return fail(STAG_KDE_EINVAL, "an index is outside [0, n)");
-    if (W)
-        for (int64_t p = 0; p < nnz; ++p)
-            if (!(W[p] >= 0.f) || !isfinite(W[p])) return fail(STAG_KDE_EINVAL, "weights must be finite and >= 0");
     if (!host_values_ok(Q, m * h->d)) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
+    // (the offsets are checked here because the kernel's reads depend on them; the
+    // indices and weights are checked on the device, beside the sum, before out is written)
     DeviceGuard g(h->device);
     if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
     // one device buffer: offsets | indices | weights | queries (16-byte aligned parts)
@@ -432,11 +429,17 @@ int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_
     if (nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dIdx, idx, nnz * 8, cudaMemcpyHostToDevice, s));
     if (W && nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dW, W, nnz * 4, cudaMemcpyHostToDevice, s));
     STAG_CUDA_TRY(cudaMemcpyAsync(dQ, Q, m * h->d * 4, cudaMemcpyHostToDevice, s));
-    rc = subset_query(h, dQ, m, dOff, dIdx, W ? dW : nullptr, h->out_dev, s, (double)nnz);
+    STAG_CUDA_TRY(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
+    rc = subset_check_entries(dIdx, W ? dW : nullptr, nnz, h->n, h->flag_dev, s);
+    if (!rc) rc = subset_query(h, dQ, m, dOff, dIdx, W ? dW : nullptr, h->out_dev, s, (double)nnz);
     if (rc) {
         cudaStreamSynchronize(s);
         return rc;
     }
+    STAG_CUDA_TRY(cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*h->flag_host & 1) return fail(STAG_KDE_EINVAL, "an index is outside [0, n)");
+    if (*h->flag_host & 2) return fail(STAG_KDE_EINVAL, "weights must be finite and >= 0");
     STAG_CUDA_TRY(cudaMemcpyAsync(out, h->out_dev, m * 8, cudaMemcpyDeviceToHost, s));
     STAG_CUDA_TRY(cudaStreamSynchronize(s));
     return 0;
