@@ -863,59 +863,66 @@ __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, in
     }
 }
 
-// FP16 hi/lo split of u = (q - c_g) * scale_u for m_pad rows (padding rows zero). A query
-// farther from the data than the split's range is zeroed and marked in qbad; the combine
-// hands it to the plain FP32 form.
-__global__ void tc_split_queries_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int Kp, int64_t m_pad,
-                                        const float *__restrict__ cg, const float *__restrict__ scales,
-                                        __half *__restrict__ ahi, __half *__restrict__ alo, int *__restrict__ qbad) {
-    const double su = scales[1];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_pad * Kp;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = i / Kp;
-        const int k = (int)(i % Kp);
-        __half h = __float2half_rn(0.f), l = __float2half_rn(0.f);
-        if (r < m && k < d) {
-            const double u = ((double)Q[r * d + k] - (double)cg[k]) * su;
-            if (fabs(u) < 0x1p15) {
-                h = __double2half(u);
-                l = __double2half(u - (double)__half2float(h));
-            } else {
-                qbad[r] = 1;
-            }
-        }
-        ahi[i] = h;
-        alo[i] = l;
-    }
-}
-
 // R[t][q] = c * ||q - c_t||^2 by direct differences in FP32 (padding queries: 0), the
-// per-query upper bound on every exponent, and ||q - c_g||.
+// per-query upper bound on every exponent, and ||q - c_g||. The first column of blocks
+// also writes the query's scaled, centred coordinates u = (q - c_g) * scale_u as FP16
+// hi/lo pairs (the MMA's A operand; the difference and scale in FP64, u_lo = u - u_hi)
+// and flags, in qbad, a query farther from the data than that range (its row is zeroed and
+// the combine hands it to the plain FP32 form).
 // One thread per query (its coordinates in registers), 128 queries per block, the tile
 // centres of a group of 32 tiles staged in shared memory and read as broadcasts.
 template <int KP>
 __global__ void __launch_bounds__(128)
 tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_pad, const float *__restrict__ cent,
                   int64_t T, int tiles_per_block, float c, float *__restrict__ R, const float *__restrict__ cg,
-                  float *__restrict__ unorm, const float *__restrict__ tinfo, unsigned *__restrict__ ub) {
+                  float *__restrict__ unorm, const float *__restrict__ tinfo, unsigned *__restrict__ ub,
+                  const float *__restrict__ scales, __half *__restrict__ ahi, __half *__restrict__ alo,
+                  int *__restrict__ qbad) {
     constexpr int TG = 32;  // tiles per shared-memory group
     __shared__ __align__(16) float sc[TG][KP];
     __shared__ float srad[TG];
     const int64_t q0 = (int64_t)blockIdx.x * 128;
     const int r = threadIdx.x;
     const bool real = q0 + r < m;
+    if (blockIdx.y == 0) {
+        // ||q - c_g|| and the A operand: FP16 hi/lo splits of u, zero for padding rows and
+        // coordinates, stored eight coordinates (16 bytes) at a time
+        const double su = scales[1];
+        float s = 0.f;
+        bool bad = false;
+        uint4 *dh = reinterpret_cast<uint4 *>(ahi + (q0 + r) * KP);
+        uint4 *dl = reinterpret_cast<uint4 *>(alo + (q0 + r) * KP);
+#pragma unroll 1
+        for (int k8 = 0; k8 < KP / 8; ++k8) {
+            __align__(16) __half hv[8], lv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int k = k8 * 8 + j;
+                __half hh = __float2half_rn(0.f), ll = __float2half_rn(0.f);
+                if (real && k < d) {
+                    const float qk = Q[(q0 + r) * d + k];
+                    const float df = qk - cg[k];
+                    s = fmaf(df, df, s);
+                    const double u = ((double)qk - (double)cg[k]) * su;
+                    if (fabs(u) < 0x1p15) {
+                        hh = __float2half_rn((float)u);
+                        ll = __float2half_rn((float)(u - (double)__half2float(hh)));
+                    } else {
+                        bad = true;
+                    }
+                }
+                hv[j] = hh;
+                lv[j] = ll;
+            }
+            dh[k8] = *reinterpret_cast<const uint4 *>(hv);
+            dl[k8] = *reinterpret_cast<const uint4 *>(lv);
+        }
+        unorm[q0 + r] = real ? sqrtf(s) : 0.f;
+        if (bad) qbad[q0 + r] = 1;
+    }
     float qv[KP];
 #pragma unroll
     for (int k = 0; k < KP; ++k) qv[k] = (real && k < d) ? Q[(q0 + r) * d + k] : 0.f;
-    if (blockIdx.y == 0) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
-            const float df = qv[k] - cg[k];
-            s = fmaf(df, df, s);
-        }
-        unorm[q0 + r] = real ? sqrtf(s) : 0.f;
-    }
     // the query as packed coordinate pairs: two differences and two FMAs per instruction
     uint64_t qp[KP / 2];
 #pragma unroll
@@ -1272,7 +1279,7 @@ int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit) {
     return 0;
 }
 
-// Query-side preparation: FP16 splits of the queries, the row terms and bounds.
+// Query-side preparation: FP16 splits of the queries, the row terms and bounds (one launch).
 static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     TcData *tc = h->tc;
     const int Kp = tc->Kp;
@@ -1280,16 +1287,15 @@ static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     const double c = h->a * 1.4426950408889634;
     STAG_CUDA_TRY(cudaMemsetAsync(tc->qbad, 0, m_pad * sizeof(int), s));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->ub, 0, m_pad * sizeof(unsigned), s));
-    count_launch(2);
-    tc_split_queries_kernel<<<grid_for(m_pad * Kp, 256), 256, 0, s>>>(dQ, m, h->d, Kp, m_pad, tc->cg, tc->scales,
-                                                                      tc->a_hi, tc->a_lo, tc->qbad);
+    count_launch(1);
     const int tpb = 64;
     dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
     switch (Kp) {
 #define STAG_ROWTERM(KPV)                                                                                          \
     case KPV:                                                                                                      \
         tc_rowterm_kernel<KPV><<<grid, 128, 0, s>>>(dQ, m, h->d, m_pad, tc->cent, tc->T, tpb, (float)c, tc->rowterm, \
-                                                    tc->cg, tc->unorm, tc->tinfo, tc->ub);                         \
+                                                    tc->cg, tc->unorm, tc->tinfo, tc->ub, tc->scales, tc->a_hi,    \
+                                                    tc->a_lo, tc->qbad);                                           \
         break;
         STAG_ROWTERM(16)
         STAG_ROWTERM(32)
