@@ -132,20 +132,29 @@ class ClockSampler:
 # CPU baseline (the FP64 oracle, as it stands)
 # ------------------------------------------------------------------------------------
 def cpu_oracle_rate(X, Q, a, budget_s=12.0, min_q=2, kernel="gaussian"):
+    """The oracle's rate on the host cores over the first s queries, for one bandwidth or
+    a list of (bandwidth, kernel) pairs (each over the same s queries); s is sized from
+    the marginal per-query time of two probes so that the sample takes about budget_s."""
     import oracle
+    pairs = list(a) if isinstance(a, (list, tuple)) else [(a, kernel)]
     threads = os.cpu_count() or 1
-    q0 = max(min_q, threads)
-    t = time.perf_counter()
-    oracle.kde_kernel(X, Q[:q0], a, kernel, threads=threads)
-    dt = time.perf_counter() - t
-    per_q = dt / q0
-    s = int(min(len(Q), max(q0, budget_s / max(per_q, 1e-9))))
+    q1 = min(len(Q), max(min_q, threads))
+    q2 = min(len(Q), 4 * q1)
+
+    def run(cnt):
+        t = time.perf_counter()
+        for ab, kn in pairs:
+            oracle.kde_kernel(X, Q[:cnt], ab, kn, threads=threads)
+        return time.perf_counter() - t
+
+    t1, t2 = run(q1), run(q2)
+    per_q = (t2 - t1) / (q2 - q1) if q2 > q1 and t2 > t1 else t2 / q2
+    s = int(min(len(Q), max(q2, budget_s / max(per_q, 1e-9))))
     s = max(threads, (s // threads) * threads) if s >= threads else s
-    t = time.perf_counter()
-    oracle.kde_kernel(X, Q[:s], a, kernel, threads=threads)
-    dt = time.perf_counter() - t
-    return {"value": s * X.shape[0] / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {s} queries x all {X.shape[0]} points, d={X.shape[1]}, a={a}, {kernel} kernel, FP64, "
+    dt = run(s)
+    bw = ", ".join(f"a={ab} ({kn})" for ab, kn in pairs)
+    return {"value": s * X.shape[0] * len(pairs) / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first {s} queries x all {X.shape[0]} points, d={X.shape[1]}, FP64, for each of {bw}; "
                       f"{dt:.1f} s"}
 
 
@@ -440,8 +449,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(X, Q, alist[len(alist) // 2], budget_s=args.cpu_budget,
-                              kernel=kernels[len(alist) // 2])
+        cpu = cpu_oracle_rate(X, Q, list(zip(alist, kernels)), budget_s=args.cpu_budget)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -861,7 +869,7 @@ def main():
     ap.add_argument("--form", default="auto", choices=["auto", "tc", "simt_f32"])
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--m", type=int, default=None)
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
