@@ -676,7 +676,10 @@ def run_lsh(args):
                            "parallelism": f"replicas x{world} (query batches)"},
                 "create_ms": create_ms, "gpu_launches": int(launches),
                 "roofline": {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
-                             "note": "sort- and scan-dominated (radix passes over the raw candidate lists); "
+                             "note": "latency-bound per-query passes (bucket lookups, then a counting and a "
+                                     "writing pass over a shared-memory bitmap of the points); the lists written "
+                                     f"({8 * cands / 1e6:.0f} MB per call) move at "
+                                     f"{8 * cands / (total_ms * 1e-3 / args.steps) / 1e9:.0f} GB/s; "
                                      f"{cands / (total_ms * 1e-3 / args.steps) / 1e9:.2f}e9 distinct candidates/s"},
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}

@@ -14,9 +14,13 @@
 // K-tuples mapping to the same 58-bit key would merge buckets (probability ~n^2 2^-59).
 //
 // Query: hash the queries, binary-search each table for the query's key (one thread per
-// (query, table)), list every bucket member (one warp per query), then remove repeats
-// across tables: a radix sort of (query << 32 | index) keys and a per-query unique pass,
-// so every query gets its distinct candidates in increasing index order.
+// (query, table)), then remove repeats across tables so that every query gets its
+// distinct candidates in increasing index order. Up to 2^22 points, a block takes one
+// (query, slice of at most 1572864 points) at a time, sets a bit per bucket member in a
+// shared-memory bitmap of the slice and walks it in index order (a counting pass, a
+// prefix sum over the items, a writing pass). Beyond that, every bucket member is listed
+// (one warp per query) and repeats are removed by a radix sort of (query << 32 | index)
+// keys and a per-query unique pass.
 #include <stdint.h>
 
 #include <algorithm>
@@ -120,7 +124,7 @@ __global__ void lsh_lookup_kernel(const int32_t *__restrict__ HQ, int64_t m, int
         const int64_t hi = lower_bound(keys, lo, (l + 1) * n, key + 1);
         range[2 * e] = lo;
         range[2 * e + 1] = hi;
-        if (hi > lo) atomicAdd(&count[j], (unsigned long long)(hi - lo));
+        if (count && hi > lo) atomicAdd(&count[j], (unsigned long long)(hi - lo));
     }
 }
 
@@ -190,6 +194,111 @@ __global__ void lsh_unique_kernel(const uint64_t *__restrict__ raw, const int64_
     }
 }
 
+constexpr int kBmThreads = 1024;
+constexpr int64_t kMaxSliceWords = 49152;  // bitmap words per work item at most (1572864 points, 192 KB)
+// Beyond 2^22 points (16 slices, each re-reading the query's bucket members) the sort
+// path is used.
+constexpr int64_t kBmMaxPoints = (int64_t)1 << 22;
+
+// Words of the bitmap over n points, the number of slices it is cut into (as few as fit
+// in shared memory: every slice re-reads the query's bucket members) and their size.
+int64_t bitmap_words(int64_t n) { return (n + 31) / 32; }
+int64_t bitmap_slices(int64_t n) { return (bitmap_words(n) + kMaxSliceWords - 1) / kMaxSliceWords; }
+int64_t bitmap_slice_words(int64_t n) { return (bitmap_words(n) + bitmap_slices(n) - 1) / bitmap_slices(n); }
+bool bitmap_fits(int64_t n) { return n <= kBmMaxPoints; }
+
+// Exclusive prefix sum of c over the block's threads (thread order); *total gets the sum.
+__device__ __forceinline__ int block_exclusive_scan(int c, int *warp_sums, int *total) {
+    constexpr int kWarps = kBmThreads >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_sums[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < kWarps ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        if (lane < kWarps) warp_sums[lane] = v;  // inclusive prefix over warps
+    }
+    __syncthreads();
+    const int before = (warp > 0 ? warp_sums[warp - 1] : 0) + inc - c;
+    *total = warp_sums[kWarps - 1];
+    return before;
+}
+
+// Distinct candidates of each query from its L bucket ranges, through a bitmap of the
+// points in shared memory. A work item is (query j, slice s): the points
+// [s * 32 * sw, (s + 1) * 32 * sw) (sw words per slice; one slice up to 1572864 points);
+// items are taken grid-stride, slice fastest, so that the slices of one query read its
+// bucket members while they are in L2. Every bucket member inside the slice sets its bit (one warp per table), then each
+// thread walks a contiguous run of words in index order. Pass kWrite = false writes the
+// number of distinct candidates per item to ucount; kWrite = true writes them, increasing,
+// at out[item_off[item] ..], so a query's list is its slices' lists in slice order.
+template <bool kWrite, bool kSliced>
+__global__ void __launch_bounds__(kBmThreads)
+lsh_bitmap_kernel(const int64_t *__restrict__ range, int64_t m, int L, const uint32_t *__restrict__ ids,
+                  int64_t words, int64_t slices, int64_t sw, unsigned long long *__restrict__ ucount,
+                  const int64_t *__restrict__ item_off, int64_t *__restrict__ out) {
+    extern __shared__ uint32_t bm[];  // [sw] bitmap words, then 32 ints of scan scratch
+    int *warp_sums = reinterpret_cast<int *>(bm + sw);
+    const int tid = threadIdx.x;
+    // an odd run length keeps the 32 lanes' words in 32 different banks
+    const int64_t per = ((sw + kBmThreads - 1) / kBmThreads) | 1;
+    const int64_t items = m * slices;
+    for (int64_t w = tid; w < sw; w += kBmThreads) bm[w] = 0u;
+    __syncthreads();
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        // (one slice: the item is the query, every member's bit is in the bitmap)
+        const int64_t j = kSliced ? it / slices : it;
+        const int64_t wbase = kSliced ? (it % slices) * sw : 0;
+        const int64_t wn = kSliced ? min(sw, words - wbase) : words;  // words of this slice
+        const uint32_t ilo = (uint32_t)(wbase * 32), ihi = (uint32_t)((wbase + wn) * 32);
+        // one warp per table (the tables' loads are in flight together), lanes over members
+        for (int l = tid >> 5; l < L; l += kBmThreads >> 5) {
+            const int64_t lo = range[2 * (j * L + l)], hi = range[2 * (j * L + l) + 1];
+            for (int64_t p = lo + (tid & 31); p < hi; p += 32) {
+                const uint32_t i = ids[p];
+                if (!kSliced || (i >= ilo && i < ihi)) atomicOr(&bm[(i - ilo) >> 5], 1u << (i & 31));
+            }
+        }
+        __syncthreads();
+        const int64_t w0 = min(wn, (int64_t)tid * per), w1 = min(wn, w0 + per);
+        int c = 0;
+        for (int64_t w = w0; w < w1; ++w) c += __popc(bm[w]);
+        int total = 0;
+        const int before = block_exclusive_scan(c, warp_sums, &total);
+        if (kWrite) {
+            int64_t pos = item_off[it] + before;
+            for (int64_t w = w0; w < w1; ++w) {
+                uint32_t v = bm[w];
+                while (v) {
+                    out[pos++] = (int64_t)ilo + w * 32 + (__ffs(v) - 1);
+                    v &= v - 1u;
+                }
+            }
+        } else if (tid == 0) {
+            ucount[it] = (unsigned long long)total;
+        }
+        for (int64_t w = w0; w < w1; ++w) bm[w] = 0u;
+        __syncthreads();  // cleared, and the scan scratch is free again
+    }
+}
+
+// dOff[j] = item_off[j * slices] for j = 0..m (a query's list starts at its first slice).
+__global__ void lsh_item_to_query_off_kernel(const int64_t *__restrict__ item_off, int64_t m, int64_t slices,
+                                             int64_t *__restrict__ dOff) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j <= m; j += (int64_t)gridDim.x * blockDim.x)
+        dOff[j] = item_off[j * slices];
+}
+
 int grow(void **p, int64_t *cap, int64_t bytes) {
     if (*cap >= bytes) return 0;
     cudaFree(*p);
@@ -230,8 +339,61 @@ int bits_for(int64_t v) {
     return b;
 }
 
+// The bitmap path of lsh_run: bucket ranges, distinct counts per (query, slice), their
+// prefix sum, the lists, and the per-query offsets. Synchronises the stream.
+int lsh_run_bitmap(stag_lsh *h, const int32_t *HQ, int64_t *range, int64_t m, int64_t *dOff, cudaStream_t s,
+                   int64_t *total) {
+    const int64_t words = bitmap_words(h->n), slices = bitmap_slices(h->n), items = m * slices;
+    const int64_t sw = bitmap_slice_words(h->n);
+    const size_t smem = (size_t)(sw + 32) * 4;
+    constexpr int kMaxSmem = (int)((kMaxSliceWords + 32) * 4);
+    static const cudaError_t attr = [] {
+        cudaError_t e = cudaFuncSetAttribute(lsh_bitmap_kernel<false, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(lsh_bitmap_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(lsh_bitmap_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(lsh_bitmap_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kMaxSmem);
+        return e;
+    }();
+    STAG_CUDA_TRY(attr);
+    auto count_k = slices > 1 ? lsh_bitmap_kernel<false, true> : lsh_bitmap_kernel<false, false>;
+    auto write_k = slices > 1 ? lsh_bitmap_kernel<true, true> : lsh_bitmap_kernel<true, false>;
+    const int64_t b_cnt = round_up(items * 8, 256), b_off = round_up((items + 1) * 8, 256);
+    int rc = grow(&h->sort_buf, &h->sort_cap, b_cnt + b_off);
+    if (rc) return rc;
+    unsigned long long *ucount = (unsigned long long *)h->sort_buf;
+    int64_t *item_off = (int64_t *)((char *)h->sort_buf + b_cnt);
+    int dev_sms = 0;
+    STAG_CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)dev_sms * 2));
+    count_launch(4);
+    lsh_lookup_kernel<<<grid_for_elems(m * h->L, 256), 256, 0, s>>>(HQ, m, h->K, h->L, h->keys, h->n, range, nullptr);
+    count_k<<<grid, kBmThreads, smem, s>>>(range, m, h->L, h->ids, words, slices, sw, ucount, nullptr, nullptr);
+    scan_i64_kernel<<<1, 1024, 0, s>>>(ucount, items, item_off);
+    lsh_item_to_query_off_kernel<<<grid_for_elems(m + 1, 256), 256, 0, s>>>(item_off, m, slices, dOff);
+    STAG_CUDA_TRY(cudaGetLastError());
+    int64_t U = 0;
+    STAG_CUDA_TRY(cudaMemcpyAsync(&U, dOff + m, 8, cudaMemcpyDeviceToHost, s));
+    STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    rc = grow(&h->cand, &h->cand_cap, std::max<int64_t>(U, 1) * 8);
+    if (rc) return rc;
+    count_launch();
+    write_k<<<grid, kBmThreads, smem, s>>>(range, m, h->L, h->ids, words, slices, sw, nullptr, item_off,
+                                           (int64_t *)h->cand);
+    STAG_CUDA_TRY(cudaGetLastError());
+    STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    *total = U;
+    return 0;
+}
+
 // Candidate lists of the device queries dQ into dOff (m + 1, device) and the handle's
-// candidate buffer; *total = number of candidates. Synchronises the stream twice.
+// candidate buffer; *total = number of candidates. Synchronises the stream.
 int lsh_run(stag_lsh *h, const float *dQ, int64_t m, int64_t *dOff, cudaStream_t s, int64_t *total) {
     const int L = h->L, K = h->K;
     const int64_t nf = (int64_t)K * L;
@@ -247,6 +409,7 @@ int lsh_run(stag_lsh *h, const float *dQ, int64_t m, int64_t *dOff, cudaStream_t
     int64_t *raw_off = (int64_t *)(base + b_hq + b_rng + b_cnt);
     rc = launch_hash(h, dQ, m, HQ, s);
     if (rc) return rc;
+    if (bitmap_fits(h->n)) return lsh_run_bitmap(h, HQ, range, m, dOff, s, total);
     STAG_CUDA_TRY(cudaMemsetAsync(count, 0, m * 8, s));
     count_launch(2);
     lsh_lookup_kernel<<<grid_for_elems(m * L, 256), 256, 0, s>>>(HQ, m, K, L, h->keys, h->n, range, count);

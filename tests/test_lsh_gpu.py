@@ -112,6 +112,43 @@ def test_pipeline_into_subset_sums():
 
 
 @pytest.mark.slow
+def test_sort_path_beyond_the_bitmap():
+    # n above what the shared-memory bitmap path serves (2^22 points): repeats across
+    # tables are removed by the radix-sort path instead; the lists are the same
+    E = _cls()
+    r = np.random.default_rng(17)
+    X = r.normal(scale=40.0, size=(4_500_000, 2)).astype(np.float32)
+    Q = r.normal(scale=40.0, size=(40, 2)).astype(np.float32)
+    with E(X, 4, 3, seed=17) as lsh:
+        off, idx = lsh.query(Q)
+        A, B = lsh.A, lsh.B
+    woff, widx = oracle.lsh_candidates(oracle.lsh_hash(X, A, B), oracle.lsh_hash(Q, A, B), 4, 3)
+    assert woff[-1] > 1000
+    assert np.array_equal(off, woff)
+    assert np.array_equal(idx, widx)
+
+
+@pytest.mark.slow
+def test_bitmap_slices_and_duplicates():
+    # n spanning two slices of the bitmap path (at most 1572864 points each), with every
+    # point repeated three times (identical hash values: the same buckets)
+    E = _cls()
+    r = np.random.default_rng(18)
+    base = r.normal(scale=6.0, size=(600_000, 3)).astype(np.float32)
+    X = np.concatenate([base, base[::-1], base])
+    Q = np.concatenate([base[:30], r.normal(scale=6.0, size=(30, 3)).astype(np.float32)])
+    with E(X, 3, 4, seed=18) as lsh:
+        off, idx = lsh.query(Q)
+        A, B = lsh.A, lsh.B
+    woff, widx = oracle.lsh_candidates(oracle.lsh_hash(X, A, B), oracle.lsh_hash(Q, A, B), 3, 4)
+    assert np.array_equal(off, woff)
+    assert np.array_equal(idx, widx)
+    lists = _lists(off, idx)
+    for j in range(30):  # a data point finds all three copies of itself
+        assert {j, len(X) - 600_000 + j, 2 * 600_000 - 1 - j} <= set(lists[j])
+
+
+@pytest.mark.slow
 def test_paper_parameters_sampled():
     # the paper's example tables (K = 6, L = 50) over 200000 points, 2000 queries; 40 lists
     # checked against the oracle
