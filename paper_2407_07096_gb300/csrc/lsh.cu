@@ -261,12 +261,21 @@ lsh_bitmap_kernel(const int64_t *__restrict__ range, int64_t m, int L, const uin
         const int64_t wbase = kSliced ? (it % slices) * sw : 0;
         const int64_t wn = kSliced ? min(sw, words - wbase) : words;  // words of this slice
         const uint32_t ilo = (uint32_t)(wbase * 32), ihi = (uint32_t)((wbase + wn) * 32);
-        // one warp per table (the tables' loads are in flight together), lanes over members
+        // one warp per table (the tables' loads are in flight together), lanes over members,
+        // four loads issued before their bits are set (indices are below n < 2^32 - 1, so
+        // the all-ones word marks an empty slot)
         for (int l = tid >> 5; l < L; l += kBmThreads >> 5) {
             const int64_t lo = range[2 * (j * L + l)], hi = range[2 * (j * L + l) + 1];
-            for (int64_t p = lo + (tid & 31); p < hi; p += 32) {
-                const uint32_t i = ids[p];
-                if (!kSliced || (i >= ilo && i < ihi)) atomicOr(&bm[(i - ilo) >> 5], 1u << (i & 31));
+            for (int64_t p = lo + (tid & 31); p < hi; p += 128) {
+                uint32_t iv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) iv[u] = p + 32 * u < hi ? ids[p + 32 * u] : 0xffffffffu;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t i = iv[u];
+                    if (i != 0xffffffffu && (!kSliced || (i >= ilo && i < ihi)))
+                        atomicOr(&bm[(i - ilo) >> 5], 1u << (i & 31));
+                }
             }
         }
         __syncthreads();
