@@ -2,7 +2,6 @@
 persistent tensor-core launch per operand width, captured in a CUDA graph. Every result
 must equal a solo query on the same handle within the form's tolerance, and match the
 FP64 oracle; replays must be bitwise identical and see new query contents."""
-import ctypes
 
 import numpy as np
 import pytest
