@@ -76,6 +76,31 @@ def test_tc_ill_conditioned_queries_are_recomputed(K):
     assert np.all(oracle.rel_err(got, ref) <= np.maximum(TOL, tol_f32(kappa, 128)))
 
 
+def test_tc_queries_beyond_the_split_range(K):
+    # queries ~1000 from a unit cloud (more than 64x the data's extent from its centre):
+    # their scaled coordinates leave FP16's range, so they are flagged and recomputed by
+    # the FP32 form; a tiny a keeps their densities far from zero
+    r = np.random.default_rng(21)
+    X = r.normal(size=(3000, 4)).astype(np.float32)
+    Q = r.normal(size=(200, 4)).astype(np.float32)
+    Q[::4, 0] += np.float32(1000.0)
+    a = 1e-6
+    with K(X, a, form="tc") as kde:
+        got = kde.query(Q)
+        redo = kde.last_recomputed()
+    ref = oracle.kde(X, Q, a)
+    assert redo >= 50
+    assert oracle.rel_err(got, ref).max() <= TOL
+    assert np.all(ref[::4] > 0.3 * 3000)
+
+
+def test_tc_normalise_option(K):
+    X, Q = mixture_inputs(22, 3000, 200, 16)
+    with K(X, 0.2, form="tc", normalise=True) as kde:
+        got = kde.query(Q)
+    assert oracle.rel_err(got, oracle.kde(X, Q, 0.2) / 3000.0).max() <= TOL
+
+
 def test_tc_a_zero_is_exactly_n(K):
     X, Q = mixture_inputs(3, 5001, 300, 16)
     with K(X, 0.0, form="tc") as kde:
