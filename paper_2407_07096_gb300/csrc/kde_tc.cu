@@ -55,6 +55,7 @@
 
 #include "f32x2.cuh"
 #include "internal.h"
+#include "kernel_fn.cuh"
 #include "sm100_ptx.cuh"
 
 namespace stagkde {
@@ -73,6 +74,7 @@ struct TcData {
     float *tinfo = nullptr;                   // [T][4]: tile RMS radius, 0, 0, 0
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
     float *cg = nullptr;                      // [Kp]: global centre c_g
+    float *xs = nullptr;                      // [n][d]: the points in tile (k-d) order, FP32 row-major
     double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
     unsigned *vmax_bits = nullptr;            // max |x_k - c_t,k| (float bits)
     unsigned *xmax_bits = nullptr;            // max |x_k - c_g,k| (float bits)
@@ -964,6 +966,151 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
     if (tb > ta) atomicMax(ub + q0 + r, float_order_bits(real ? ubest : 0.f));
 }
 
+// FP32 recompute of the queries the tensor-core estimate flags, over the tiles that can
+// matter only. Per query, from the row terms R_t = c ||q - c_t||^2 and the tiles' max
+// radii rho_t (c = a log2 e, exponents in log2 units):
+//     ub_t = -(max(0, sqrt(R_t) - sqrt(c) rho_t))^2  >= every exponent -c ||q - x||^2 in tile t
+//     lb_t = -(sqrt(R_t) + sqrt(c) rho_t)^2          <= the largest exponent in tile t
+// (with a 1e-5 relative slack on sqrt(R_t) for rounding), so LB = max_t lb_t bounds the
+// row's largest term from below, and a tile with ub_t < LB - 64 holds only terms below
+// 2^-64 of it: all of them together change the sum by less than n 2^-64 relative, and
+// the tile is skipped. The others are evaluated like the plain FP32 form (direct
+// differences in FP32, one ex2 per pair, a per-lane power-of-two shift raised when a term
+// would pass 2^64, FP32 partial sums flushed to FP64 every 16 terms, merged in FP64 in a
+// fixed order). One block of 8 warps per flagged query (grid-stride over the device
+// count): tiles are bounded 32 at a time (one ballot), warp w takes every 8th included
+// tile of each group of 32, its lanes split the tile's points.
+constexpr int kPrunedWarps = 8;
+constexpr float kPruneLog2 = 64.f;
+// Above this d the distances concentrate (few tiles drop out) and the plain kernel's
+// register-tiled form does the recompute faster.
+constexpr int64_t kPrunedMaxD = 16;
+
+template <bool kVec4>
+__global__ void __launch_bounds__(32 * kPrunedWarps)
+tc_fixup_pruned_kernel(const float *__restrict__ Q, int d, const int *__restrict__ fix_idx,
+                       const int *__restrict__ fix_count, int64_t m_pad, const float *__restrict__ R,
+                       const float *__restrict__ tinfo, const float *__restrict__ xs, int64_t n, int64_t T, int BN,
+                       float c, double scale, double *__restrict__ out) {
+    extern __shared__ __align__(16) float sq[];  // [d] query, then the warps' partials
+    double *wsum = reinterpret_cast<double *>(sq + ((d + 3) & ~3));
+    float *wshift = reinterpret_cast<float *>(wsum + kPrunedWarps);
+    float *wlb = wshift + kPrunedWarps;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cnt = *fix_count;
+    const float sqc = sqrtf(c), negc = -c;
+    constexpr float kShiftInit = -0x1p100f, kGuard = 0x1p64f;
+    auto bounds = [&](int64_t t, int64_t q, float &ub, float &lb) {
+        const float r = sqrtf(R[t * m_pad + q]);
+        const float rho = sqc * tinfo[t * 4 + 1];
+        const float g = fmaxf(0.f, r * (1.f - 1e-5f) - rho);
+        const float h2 = r * (1.f + 1e-5f) + rho;
+        ub = -g * g;
+        lb = -h2 * h2;
+    };
+    for (int64_t w = blockIdx.x; w < cnt; w += gridDim.x) {
+        const int64_t q = fix_idx[w];
+        for (int k = threadIdx.x; k < d; k += 32 * kPrunedWarps) sq[k] = Q[q * d + k];
+        // LB over all tiles
+        float lb_max = -INFINITY;
+        for (int64_t t = threadIdx.x; t < T; t += 32 * kPrunedWarps) {
+            float ub, lb;
+            bounds(t, q, ub, lb);
+            lb_max = fmaxf(lb_max, lb);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) lb_max = fmaxf(lb_max, __shfl_xor_sync(0xffffffffu, lb_max, o));
+        if (lane == 0) wlb[warp] = lb_max;
+        __syncthreads();
+        float thr = wlb[0];
+#pragma unroll
+        for (int i = 1; i < kPrunedWarps; ++i) thr = fmaxf(thr, wlb[i]);
+        thr -= kPruneLog2;
+        float shift = kShiftInit, acc32 = 0.f;
+        double acc64 = 0.0;
+        int nacc = 0;
+        for (int64_t t0 = 0; t0 < T; t0 += 32) {
+            bool keep = false;
+            if (t0 + lane < T) {
+                float ub, lb;
+                bounds(t0 + lane, q, ub, lb);
+                keep = ub >= thr;
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, keep);
+            for (int rank = 0; mask; ++rank) {
+                const int64_t t = t0 + __ffs(mask) - 1;
+                mask &= mask - 1u;
+                if (rank % kPrunedWarps != warp) continue;
+                const int64_t p1 = min(n, (t + 1) * BN);
+                for (int64_t p = t * BN + lane; p < p1; p += 32) {
+                    const float *x = xs + p * d;
+                    float d2 = 0.f;
+                    if constexpr (kVec4) {
+                        for (int k = 0; k < d; k += 4) {
+                            const float4 xv = *reinterpret_cast<const float4 *>(x + k);
+                            const float4 qv = *reinterpret_cast<const float4 *>(sq + k);
+                            float e = qv.x - xv.x;
+                            d2 = fmaf(e, e, d2);
+                            e = qv.y - xv.y;
+                            d2 = fmaf(e, e, d2);
+                            e = qv.z - xv.z;
+                            d2 = fmaf(e, e, d2);
+                            e = qv.w - xv.w;
+                            d2 = fmaf(e, e, d2);
+                        }
+                    } else {
+                        for (int k = 0; k < d; ++k) {
+                            const float e = sq[k] - x[k];
+                            d2 = fmaf(e, e, d2);
+                        }
+                    }
+                    float e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
+                    if (!(fabsf(e) <= kGuard)) {
+                        // first term, or one far above the current shift: move the shift up
+                        const float s_new = fmaxf(ceilf(negc * d2), kShiftInit);
+                        if (s_new > shift) {
+                            const int de = cexp(shift - s_new);
+                            acc32 = ldexpf(acc32, de);
+                            acc64 = ldexp(acc64, de);
+                            shift = s_new;
+                        }
+                        e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
+                    }
+                    acc32 += e;
+                    if (++nacc == 16) {
+                        acc64 += (double)acc32;
+                        acc32 = 0.f;
+                        nacc = 0;
+                    }
+                }
+            }
+        }
+        acc64 += (double)acc32;
+        // merge the lanes, then the warps: common shift = the largest, fixed order
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const double oa = __shfl_xor_sync(0xffffffffu, acc64, o);
+            const float os = __shfl_xor_sync(0xffffffffu, shift, o);
+            const float sm = fmaxf(shift, os);
+            acc64 = ldexp(acc64, cexp(shift - sm)) + ldexp(oa, cexp(os - sm));
+            shift = sm;
+        }
+        if (lane == 0) {
+            wsum[warp] = acc64;
+            wshift[warp] = shift;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float sm = wshift[0];
+            for (int i = 1; i < kPrunedWarps; ++i) sm = fmaxf(sm, wshift[i]);
+            double tot = 0.0;
+            for (int i = 0; i < kPrunedWarps; ++i) tot += ldexp(wsum[i], cexp(wshift[i] - sm));
+            out[q] = ldexp(tot, cexp(sm)) * scale;
+        }
+        __syncthreads();  // the query and the partials are free again
+    }
+}
+
 // FP64 combine of the per-split partials (as kde_combine.cu) plus the per-query error
 // estimate of the tensor-core form,
 //     est = 2^-21 * a * ||q - c_g|| * (sum_t S_t r_t) / (sum_t S_t),
@@ -1092,6 +1239,7 @@ void tc_free(stag_kde *h) {
         cudaFree(tc->tinfo);
         cudaFree(tc->cent);
         cudaFree(tc->cg);
+        cudaFree(tc->xs);
         cudaFree(tc->tsum);
         cudaFree(tc->vmax_bits);
         cudaFree(tc->xmax_bits);
@@ -1132,6 +1280,7 @@ int tc_make_view(const stag_kde *base, stag_kde *view) {
     tc->tinfo = b->tinfo;
     tc->cent = b->cent;
     tc->cg = b->cg;
+    tc->xs = b->xs;
     tc->tsum = b->tsum;
     tc->vmax_bits = b->vmax_bits;
     tc->xmax_bits = b->xmax_bits;
@@ -1163,6 +1312,8 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     STAG_CUDA_TRY(cudaMalloc(&tc->tinfo, tc->T * 4 * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->cent, tc->T * Kp * sizeof(float)));
     STAG_CUDA_TRY(cudaMalloc(&tc->cg, Kp * sizeof(float)));
+    STAG_CUDA_TRY(cudaMalloc(&tc->xs, h->n * h->d * sizeof(float)));
+    STAG_CUDA_TRY(cudaMemcpyAsync(tc->xs, dX, h->n * h->d * sizeof(float), cudaMemcpyDeviceToDevice, s));
     STAG_CUDA_TRY(cudaMalloc(&tc->tsum, tc->T * Kp * sizeof(double)));
     STAG_CUDA_TRY(cudaMalloc(&tc->vmax_bits, sizeof(unsigned)));
     STAG_CUDA_TRY(cudaMalloc(&tc->xmax_bits, sizeof(unsigned)));
@@ -1334,8 +1485,9 @@ static void fill_inst(const stag_kde *h, int64_t m, int64_t q_tiles, int64_t spl
     I->units = q_tiles * splits;
 }
 
-// FP64 combine with the per-query error estimate, then the plain-form recompute of the
-// flagged queries.
+// FP64 combine with the per-query error estimate, then the FP32 recompute of the flagged
+// queries: over the tiles that can matter (tc_fixup_pruned_kernel) for d <= 16, by the
+// plain form over all points above.
 static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
     TcData *tc = h->tc;
     const bool check = h->tc_check;
@@ -1346,7 +1498,23 @@ static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, do
         tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
     STAG_CUDA_TRY(cudaGetLastError());
     if (!check) return 0;
-    return simt_fixup_rows(h, dQ, m, tc->fix_idx, tc->fix_count, dOut, s);
+    if (h->d > kPrunedMaxD) return simt_fixup_rows(h, dQ, m, tc->fix_idx, tc->fix_count, dOut, s);
+    // low d: distances spread widely, so most tiles drop out of a flagged query's sum
+    const unsigned grid = (unsigned)(h->sm_count * 8);
+    const size_t smem = (size_t)(((h->d + 3) & ~3) * sizeof(float) + kPrunedWarps * (sizeof(double) + 2 * sizeof(float)));
+    const float c = (float)(h->a * 1.4426950408889634);
+    const double scale = h->normalise ? 1.0 / (double)h->n : 1.0;
+    count_launch();
+    if (h->d % 4 == 0)
+        tc_fixup_pruned_kernel<true><<<grid, 32 * kPrunedWarps, smem, s>>>(
+            dQ, (int)h->d, tc->fix_idx, tc->fix_count, round_up(m, BM), tc->rowterm, tc->tinfo, tc->xs, h->n, tc->T,
+            tc->BN, c, scale, dOut);
+    else
+        tc_fixup_pruned_kernel<false><<<grid, 32 * kPrunedWarps, smem, s>>>(
+            dQ, (int)h->d, tc->fix_idx, tc->fix_count, round_up(m, BM), tc->rowterm, tc->tinfo, tc->xs, h->n, tc->T,
+            tc->BN, c, scale, dOut);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
 }
 
 int tc_operand_width(const stag_kde *h) { return h->tc ? h->tc->Kp : 0; }

@@ -94,6 +94,22 @@ def test_tc_queries_beyond_the_split_range(K):
     assert np.all(ref[::4] > 0.3 * 3000)
 
 
+@pytest.mark.parametrize("a", [1.0, 4.0])
+def test_tc_pruned_recompute_of_flagged_queries(K, a):
+    # the benchmark's mixture at large a, d = 16: the queries the estimate flags are
+    # recomputed over the tiles that can matter; every query against the oracle
+    from paper_2407_07096_gb300 import datagen as G
+    X, Q = G.workload_single_d16(0, n=30_000, m=4_000)
+    with K(X, a, form="tc") as kde:
+        got = kde.query(Q)
+        redo = kde.last_recomputed()
+    ref = oracle.kde(X, Q, a)
+    if a == 4.0:
+        assert redo > 100
+    err = oracle.rel_err(got, ref)
+    assert err.max() <= TOL, err.max()
+
+
 def test_tc_normalise_option(K):
     X, Q = mixture_inputs(22, 3000, 200, 16)
     with K(X, 0.2, form="tc", normalise=True) as kde:
