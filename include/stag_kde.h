@@ -92,6 +92,11 @@ void stag_kde_opts_init(stag_kde_opts *o);
 /*
  * Creates a handle holding a device copy of X (n x d, FP32, host memory) with
  * bandwidth a. The caller may free X on return. Default options.
+ * Device memory held for the point set: the plain form's tiled copy (about n * d_pad * 4
+ * bytes, d_pad = d rounded up to 4); the tensor-core form adds the FP16 splits of the
+ * points (about n * (2 * Kp + 16) * 2 bytes, Kp = d rounded up to 16, 32, 64 or 128),
+ * per-tile centres and radii, and a k-d ordered FP32 copy (n * d * 4 bytes) from which
+ * flagged queries are recomputed. Per-query scratch comes on top (stag_kde_reserve).
  * Returns NULL on error (see stag_kde_last_error()).
  */
 stag_kde_t *stag_kde_create(const float *X, int64_t n, int64_t d, double a);
