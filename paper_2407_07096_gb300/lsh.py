@@ -62,20 +62,37 @@ class E2LSH:
         L.check(self._lib.stag_lsh_hash_dev(self._h, Q.data_ptr(), Q.shape[0], out.data_ptr(), s))
         return out
 
-    def query(self, Q):
-        """(offsets[m + 1], idx) of every query's distinct candidates, host arrays."""
+    def query(self, Q, out=None):
+        """(offsets[m + 1], idx) of every query's distinct candidates, host arrays.
+
+        out: optional (offsets, idx) host int64 arrays to fill, for instance in pinned
+        memory so that the lists come back at full copy bandwidth: offsets of at least
+        m + 1 entries, idx of any size (used when it holds every candidate, otherwise a
+        new array is made). The returned arrays are then views of them."""
         Qh = np.ascontiguousarray(np.asarray(Q, dtype=np.float32))
         if Qh.ndim != 2 or Qh.shape[1] != self.d:
             raise ValueError("Q must be m x d")
         m = Qh.shape[0]
-        off = np.zeros(m + 1, dtype=np.int64)
+        if out is None:
+            off, buf = np.zeros(m + 1, dtype=np.int64), None
+        else:
+            off, buf = out
+            for a in (off, buf):
+                if a.dtype != np.int64 or a.ndim != 1 or not a.flags.c_contiguous:
+                    raise ValueError("out arrays must be contiguous 1-D int64")
+            if off.size < m + 1:
+                raise ValueError("out offsets need m + 1 entries")
+            off = off[: m + 1]
         total = ctypes.c_int64()
-        L.check(self._lib.stag_lsh_query(self._h, Qh.ctypes.data, m, off.ctypes.data, None, 0,
-                                         ctypes.byref(total)))
+        cap = buf.size if buf is not None else 0
+        L.check(self._lib.stag_lsh_query(self._h, Qh.ctypes.data, m, off.ctypes.data,
+                                         buf.ctypes.data if cap else None, cap, ctypes.byref(total)))
+        if buf is not None and cap >= total.value:
+            return off, buf[: total.value]
         idx = np.empty(max(total.value, 1), dtype=np.int64)
         if total.value:  # the lists the call kept, without recomputing them
             L.check(self._lib.stag_lsh_fetch(self._h, idx.ctypes.data, idx.size))
-        return off, idx[:total.value]
+        return off, idx[: total.value]
 
     def query_dev(self, Q, stream=None):
         """(offsets, idx) CUDA int64 tensors of every query's distinct candidates."""

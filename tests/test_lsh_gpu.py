@@ -59,6 +59,12 @@ def test_device_entry_point_edges_and_identical_points():
         off_d, idx_d = lsh.query_dev(torch.from_numpy(Q).cuda())
         torch.cuda.synchronize()
         assert np.array_equal(off_d.cpu().numpy(), off_h) and np.array_equal(idx_d.cpu().numpy(), idx_h)
+        # caller-provided output arrays (large enough, then too small for the lists)
+        ob, ib = np.full(70, -1, np.int64), np.full(len(idx_h) + 5, -1, np.int64)
+        o2, i2 = lsh.query(Q, out=(ob, ib))
+        assert np.array_equal(o2, off_h) and np.array_equal(i2, idx_h) and np.shares_memory(i2, ib)
+        o3, i3 = lsh.query(Q, out=(ob, np.zeros(3, np.int64)))
+        assert np.array_equal(o3, off_h) and np.array_equal(i3, idx_h)
         o0, i0 = lsh.query(Q[:0])
         assert o0.tolist() == [0] and len(i0) == 0
         # every data point finds itself
