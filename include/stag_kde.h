@@ -142,10 +142,10 @@ int stag_kde_query_dev(stag_kde_t *h, const void *dQ, int64_t m, double *dOut, v
  * handles of any form (the point set is gathered from a row-major copy built on the
  * first call); FP64 handles return STAG_KDE_EUNSUPPORTED.
  *
- * Host variant: all buffers in host memory, synchronous; validates everything (offsets
- * and Q on the host before any work, indices in [0, n) and finite W >= 0 on the device
- * before the results are copied out) and returns STAG_KDE_EINVAL on a violation with out
- * untouched.
+ * Host variant: all buffers in host memory (pinned memory copies fastest), synchronous;
+ * validates everything (the offsets on the host before any work; Q finite, indices in
+ * [0, n) and finite W >= 0 on the device before the results are copied out) and returns
+ * STAG_KDE_EINVAL on a violation with out untouched.
  */
 int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_t *off, const int64_t *idx,
                           const float *W, double *out);

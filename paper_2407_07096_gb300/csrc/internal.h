@@ -89,6 +89,8 @@ struct stag_kde {
     void *sub_dev = nullptr;  // host subset call: device copies of offsets, indices, weights
     int64_t sub_dev_cap = 0;  // bytes
     int *flag_dev = nullptr;  // input-validation flag
+    cudaStream_t copy_stream[2] = {nullptr, nullptr};  // host subset call: extra streams for the list copies
+    cudaEvent_t copy_done[2] = {nullptr, nullptr};
     int *flag_host = nullptr; // pinned mirror
     int sm_count = 0;
 
@@ -123,7 +125,7 @@ int simt_reserve(stag_kde *h, int64_t m);
 int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
                     cudaStream_t s);
 int ensure_qt(stag_kde *h, int64_t floats);
-int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s);
+int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s, int bit = 1);
 int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s);
 
 // kde_subset.cu: weighted subset sums over per-query (index, weight) lists. `entries`

@@ -272,15 +272,16 @@ __global__ void to_tiles_kernel(const T *__restrict__ src, int64_t rows, int64_t
     }
 }
 
+// ORs `bit` into *flag when a value is not finite or exceeds 1e15 in magnitude.
 template <typename T>
-__global__ void check_finite_kernel(const T *__restrict__ p, int64_t count, int *flag) {
+__global__ void check_finite_kernel(const T *__restrict__ p, int64_t count, int *flag, int bit) {
     int bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double v = (double)p[i];
         bad |= !(fabs(v) <= 1e15);
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, bit);
 }
 
 // FP64 form: one thread per query, points staged through shared memory, summed in
@@ -377,10 +378,10 @@ int ensure_qt(stag_kde *h, int64_t floats) {
     return 0;
 }
 
-int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s) {
+int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s, int bit) {
     if (count <= 0) return 0;
     count_launch();
-    check_finite_kernel<float><<<grid_for(count, 256), 256, 0, s>>>(p, count, dflag);
+    check_finite_kernel<float><<<grid_for(count, 256), 256, 0, s>>>(p, count, dflag, bit);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -388,7 +389,7 @@ int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStrea
 int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s) {
     if (count <= 0) return 0;
     count_launch();
-    check_finite_kernel<double><<<grid_for(count, 256), 256, 0, s>>>(p, count, dflag);
+    check_finite_kernel<double><<<grid_for(count, 256), 256, 0, s>>>(p, count, dflag, 1);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }

@@ -123,6 +123,10 @@ void free_handle(stag_kde *h) {
     cudaFree(h->part.shift);
     cudaFree(h->flag_dev);
     if (h->flag_host) cudaFreeHost(h->flag_host);
+    for (int i = 0; i < 2; ++i) {
+        if (h->copy_done[i]) cudaEventDestroy(h->copy_done[i]);
+        if (h->copy_stream[i]) cudaStreamDestroy(h->copy_stream[i]);
+    }
     for (cudaEvent_t e : h->prof_events) cudaEventDestroy(e);
     for (cudaEvent_t e : h->prof_pool) cudaEventDestroy(e);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -409,9 +413,9 @@ int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_
         if (off[j + 1] < off[j]) return fail(STAG_KDE_EINVAL, "offsets must be non-decreasing");
     const int64_t nnz = off[m];
     if (nnz > 0 && !idx) return fail(STAG_KDE_EINVAL, "idx is NULL");
-    if (!host_values_ok(Q, m * h->d)) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
-    // (the offsets are checked here because the kernel's reads depend on them; the
-    // indices and weights are checked on the device, beside the sum, before out is written)
+    // (the offsets are checked here because the kernel's reads depend on them; Q, the
+    // indices and the weights are checked on the device, beside the sum, before out is
+    // written)
     DeviceGuard g(h->device);
     if (!g.ok) return fail(STAG_KDE_ECUDA, "cudaSetDevice failed");
     // one device buffer: offsets | indices | weights | queries (16-byte aligned parts)
@@ -425,19 +429,36 @@ int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_
     int64_t *dOff = (int64_t *)base, *dIdx = (int64_t *)(base + b_off);
     float *dW = (float *)(base + b_off + b_idx), *dQ = (float *)(base + b_off + b_idx + b_w);
     cudaStream_t s = h->stream;
+    // the index list goes up in two halves on two more streams, beside the rest on the
+    // handle's stream, so that several copy engines move the lists
+    for (int i = 0; i < 2; ++i) {
+        if (!h->copy_stream[i]) STAG_CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream[i], cudaStreamNonBlocking));
+        if (!h->copy_done[i]) STAG_CUDA_TRY(cudaEventCreateWithFlags(&h->copy_done[i], cudaEventDisableTiming));
+    }
+    const int64_t half = nnz / 2;
+    if (half > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dIdx, idx, half * 8, cudaMemcpyHostToDevice, h->copy_stream[0]));
+    if (nnz > half)
+        STAG_CUDA_TRY(cudaMemcpyAsync(dIdx + half, idx + half, (nnz - half) * 8, cudaMemcpyHostToDevice,
+                                      h->copy_stream[1]));
+    for (int i = 0; i < 2; ++i) STAG_CUDA_TRY(cudaEventRecord(h->copy_done[i], h->copy_stream[i]));
     STAG_CUDA_TRY(cudaMemcpyAsync(dOff, off, (m + 1) * 8, cudaMemcpyHostToDevice, s));
-    if (nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dIdx, idx, nnz * 8, cudaMemcpyHostToDevice, s));
     if (W && nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dW, W, nnz * 4, cudaMemcpyHostToDevice, s));
     STAG_CUDA_TRY(cudaMemcpyAsync(dQ, Q, m * h->d * 4, cudaMemcpyHostToDevice, s));
     STAG_CUDA_TRY(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
-    rc = subset_check_entries(dIdx, W ? dW : nullptr, nnz, h->n, h->flag_dev, s);
+    rc = launch_check_finite_f32(dQ, m * h->d, h->flag_dev, s, 4);
+    for (int i = 0; i < 2 && !rc; ++i) STAG_CUDA_TRY(cudaStreamWaitEvent(s, h->copy_done[i], 0));
+    if (!rc) rc = subset_check_entries(dIdx, W ? dW : nullptr, nnz, h->n, h->flag_dev, s);
     if (!rc) rc = subset_query(h, dQ, m, dOff, dIdx, W ? dW : nullptr, h->out_dev, s, (double)nnz);
     if (rc) {
+        // the caller's buffers must not be read after the return
+        cudaStreamSynchronize(h->copy_stream[0]);
+        cudaStreamSynchronize(h->copy_stream[1]);
         cudaStreamSynchronize(s);
         return rc;
     }
     STAG_CUDA_TRY(cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (*h->flag_host & 4) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
     if (*h->flag_host & 1) return fail(STAG_KDE_EINVAL, "an index is outside [0, n)");
     if (*h->flag_host & 2) return fail(STAG_KDE_EINVAL, "weights must be finite and >= 0");
     STAG_CUDA_TRY(cudaMemcpyAsync(out, h->out_dev, m * 8, cudaMemcpyDeviceToHost, s));

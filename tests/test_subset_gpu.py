@@ -113,6 +113,12 @@ def test_edge_cases_and_validation():
             with pytest.raises(L.StagKdeError) as e:
                 kde.query_subset(Q, off, idx, W)
             assert e.value.code == L.EINVAL
+        # a non-finite query coordinate (checked on the device before out is written)
+        Qbad = Q.copy()
+        Qbad[4, 2] = np.float32(np.inf)
+        with pytest.raises(L.StagKdeError) as e:
+            kde.query_subset(Qbad, np.array([0] + [1] * 9), np.array([0]))
+        assert e.value.code == L.EINVAL
         # device entry point: out-of-range entries contribute nothing
         off = np.array([0, 3, 3, 5, 6, 6, 6, 6, 6, 8], np.int64)
         idx = np.array([0, 1000, 2, -5, 7, 999, 4, 1 << 40], np.int64)
