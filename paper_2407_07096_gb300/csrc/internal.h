@@ -159,7 +159,10 @@ int tc_tile_points(int64_t d);
 int tc_prepare_points(stag_kde *h, const float *dX);
 int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s, int *dflag);
 void tc_free(stag_kde *h);
-int tc_check_error(stag_kde *h, cudaStream_t s);
+// The kernel's error code (a bounded wait that expired): tc_error_enqueue queues its copy
+// to the host on s; after s has been synchronised, tc_error_take reports and clears it.
+int tc_error_enqueue(stag_kde *h, cudaStream_t s);
+int tc_error_take(stag_kde *h, cudaStream_t s);
 int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit);
 int tc_make_view(const stag_kde *base, stag_kde *view);
 // Pieces of a tensor-core query for the batched path (kde_tc.cu).

@@ -1573,11 +1573,16 @@ int tc_fixed_rows(stag_kde *h, int64_t *count) {
     return 0;
 }
 
-int tc_check_error(stag_kde *h, cudaStream_t s) {
+int tc_error_enqueue(stag_kde *h, cudaStream_t s) {
     TcData *tc = h->tc;
     if (!tc) return 0;
     STAG_CUDA_TRY(cudaMemcpyAsync(tc->err_host, tc->err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    STAG_CUDA_TRY(cudaStreamSynchronize(s));
+    return 0;
+}
+
+int tc_error_take(stag_kde *h, cudaStream_t s) {
+    TcData *tc = h->tc;
+    if (!tc) return 0;
     if (*tc->err_host) {
         STAG_CUDA_TRY(cudaMemsetAsync(tc->err, 0, sizeof(int), s));
         return fail(STAG_KDE_ETIMEDOUT, "tensor-core kernel: a bounded wait expired");

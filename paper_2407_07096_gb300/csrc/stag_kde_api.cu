@@ -367,13 +367,20 @@ int stag_kde_query(stag_kde_t *h, const void *Q, int64_t m, double *out) {
         cudaStreamSynchronize(h->stream);
         return rc;
     }
+    // one synchronisation for both checks: the input flag and the kernel's error code
     STAG_CUDA_TRY(cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    STAG_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (*h->flag_host) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
     if (h->form == STAG_KDE_FORM_TC) {
-        rc = tc_check_error(h, h->stream);
-        if (rc) return rc;
+        rc = tc_error_enqueue(h, h->stream);
+        if (rc) {
+            cudaStreamSynchronize(h->stream);
+            return rc;
+        }
     }
+    STAG_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    // (a set error code is cleared either way; the input error is the one reported)
+    const int terr = h->form == STAG_KDE_FORM_TC ? tc_error_take(h, h->stream) : 0;
+    if (*h->flag_host) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
+    if (terr) return terr;
     STAG_CUDA_TRY(cudaMemcpyAsync(out, h->out_dev, m * 8, cudaMemcpyDeviceToHost, h->stream));
     STAG_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return 0;
