@@ -21,6 +21,8 @@
 // Other kernel functions (Sec. 3): the exponential and logistic kernels of r = sqrt(d2),
 // in the same shifted form (kernel_fn.cuh).
 //
+// Squared distances: FP32 FMA chains over blocks of 16 coordinates, block sums added
+// (about half the rounding error of a single chain at d >= 32).
 // Summation: per thread, FP32 over 16 tiles (64 terms), then FP64; the 16 threads that
 // share a row are combined in FP64 with a fixed shuffle pattern; splits of the point set
 // are combined in FP64 by kde_combine.cu. Every order is fixed, so results are
@@ -38,6 +40,7 @@ namespace {
 constexpr float kShiftFloor = -0x1p100f;  // initial shift (an exact integer)
 constexpr float kOverflowGuard = 0x1p64f;
 constexpr int kFlushTiles = 16;
+constexpr int kSumBlock = 16;  // coordinates per partial chain of a squared distance
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -164,18 +167,32 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
         const int klen = min(kSimtKC, d_pad - ch * kSimtKC);
         const float *xs = sX[stage];
         const float *qs = kSingleChunk ? sQ[0] + ch * kSimtKC * kSimtTile : sQ[kSingleChunk ? 0 : stage];
+        // blocks of kSumBlock coordinates: each block's squares are summed in a chain of
+        // its own and the block sum is added to the pair's total, which keeps the
+        // accumulated rounding error of d2 about half that of one chain over all d
+        for (int kb = 0; kb < klen; kb += kSumBlock) {
+            const int ke = min(klen, kb + kSumBlock);
+            uint64_t b2p[4][2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) b2p[i][0] = b2p[i][1] = 0ull;
 #pragma unroll 4
-        for (int k = 0; k < klen; ++k) {
-            const float4 qv = *reinterpret_cast<const float4 *>(&qs[k * kSimtTile + ty * 4]);
-            const float4 xv = *reinterpret_cast<const float4 *>(&xs[k * kSimtTile + tx * 4]);
-            const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-            const uint64_t x01 = f2::pack(xv.x, xv.y), x23 = f2::pack(xv.z, xv.w);
+            for (int k = kb; k < ke; ++k) {
+                const float4 qv = *reinterpret_cast<const float4 *>(&qs[k * kSimtTile + ty * 4]);
+                const float4 xv = *reinterpret_cast<const float4 *>(&xs[k * kSimtTile + tx * 4]);
+                const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+                const uint64_t x01 = f2::pack(xv.x, xv.y), x23 = f2::pack(xv.z, xv.w);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint64_t qq = f2::pack(qa[i], qa[i]);
+                    const uint64_t df0 = f2::sub(qq, x01), df1 = f2::sub(qq, x23);
+                    b2p[i][0] = f2::fma(df0, df0, b2p[i][0]);
+                    b2p[i][1] = f2::fma(df1, df1, b2p[i][1]);
+                }
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const uint64_t qq = f2::pack(qa[i], qa[i]);
-                const uint64_t df0 = f2::sub(qq, x01), df1 = f2::sub(qq, x23);
-                d2p[i][0] = f2::fma(df0, df0, d2p[i][0]);
-                d2p[i][1] = f2::fma(df1, df1, d2p[i][1]);
+                d2p[i][0] = f2::add(d2p[i][0], b2p[i][0]);
+                d2p[i][1] = f2::add(d2p[i][1], b2p[i][1]);
             }
         }
         __syncthreads();
@@ -361,8 +378,8 @@ int ensure_partials(stag_kde *h, int64_t entries) {
     if (h->part.sum) cudaFree(h->part.sum);
     if (h->part.shift) cudaFree(h->part.shift);
     h->part = Partials{};
-    STAG_CUDA_TRY(cudaMalloc(&h->part.sum, entries * sizeof(double)));
-    STAG_CUDA_TRY(cudaMalloc(&h->part.shift, entries * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&h->part.sum, entries * sizeof(double)));
+    STAG_CUDA_TRY(dev_malloc(&h->part.shift, entries * sizeof(float)));
     h->part.cap = entries;
     return 0;
 }
@@ -373,7 +390,7 @@ int ensure_qt(stag_kde *h, int64_t floats) {
     if (h->qt) cudaFree(h->qt);
     h->qt = nullptr;
     h->qt_cap = 0;
-    STAG_CUDA_TRY(cudaMalloc(&h->qt, floats * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&h->qt, floats * sizeof(float)));
     h->qt_cap = floats;
     return 0;
 }
@@ -398,7 +415,7 @@ int simt_prepare_points(stag_kde *h, const float *dX) {
     h->d_pad = (int)round_up(h->d, 4);
     h->n_tiles = ceil_div(h->n, kSimtTile);
     const int64_t total = h->n_tiles * h->d_pad * kSimtTile;
-    STAG_CUDA_TRY(cudaMalloc(&h->xt, total * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&h->xt, total * sizeof(float)));
     count_launch();
     to_tiles_kernel<float><<<grid_for(total, 256), 256, 0, h->stream>>>(dX, h->n, h->d, h->d_pad,
                                                                         h->n_tiles, h->xt);

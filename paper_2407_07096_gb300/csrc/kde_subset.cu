@@ -55,26 +55,37 @@ kde_subset_kernel(const float *__restrict__ X, int64_t n, int d, const float *__
             if (i < 0 || i >= n) continue;  // out-of-range entries contribute nothing
             const float w = W ? W[p] : 1.f;
             const float *x = X + i * d;
-            float d2 = 0.f;
+            // FP32 chains over blocks of 16 coordinates, block sums added (the plain
+            // form's order and error bound)
+            float d2 = 0.f, b2 = 0.f;
             if constexpr (kVec4) {
                 for (int k = 0; k < d; k += 4) {
                     const float4 xv = *reinterpret_cast<const float4 *>(x + k);
                     const float4 qv = *reinterpret_cast<const float4 *>(sq + k);
                     float t = qv.x - xv.x;
-                    d2 = fmaf(t, t, d2);
+                    b2 = fmaf(t, t, b2);
                     t = qv.y - xv.y;
-                    d2 = fmaf(t, t, d2);
+                    b2 = fmaf(t, t, b2);
                     t = qv.z - xv.z;
-                    d2 = fmaf(t, t, d2);
+                    b2 = fmaf(t, t, b2);
                     t = qv.w - xv.w;
-                    d2 = fmaf(t, t, d2);
+                    b2 = fmaf(t, t, b2);
+                    if (((k + 4) & 15) == 0) {
+                        d2 += b2;
+                        b2 = 0.f;
+                    }
                 }
             } else {
                 for (int k = 0; k < d; ++k) {
                     const float t = sq[k] - x[k];
-                    d2 = fmaf(t, t, d2);
+                    b2 = fmaf(t, t, b2);
+                    if (((k + 1) & 15) == 0) {
+                        d2 += b2;
+                        b2 = 0.f;
+                    }
                 }
             }
+            d2 += b2;
             float e = w * kfn::term<KERN>(negc, d2, shift);
             if (!(fabsf(e) <= kGuard)) {
                 // first term, or one far above the current shift: move the shift up
@@ -157,7 +168,7 @@ int subset_prepare(stag_kde *h, cudaStream_t s) {
     if (h->dtype != STAG_KDE_F32 || !h->xt) return fail(STAG_KDE_EUNSUPPORTED, "subset sums: FP32 handles only");
     if ((size_t)kSubsetWarps * h->d * sizeof(float) > 48 * 1024)
         return fail(STAG_KDE_EUNSUPPORTED, "subset sums: d too large");
-    STAG_CUDA_TRY(cudaMalloc(&h->xrow, (size_t)(h->n * h->d) * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&h->xrow, (size_t)(h->n * h->d) * sizeof(float)));
     int rc = simt_points_rows(h, h->xrow, s);
     if (rc) return rc;
     // later calls may come on other streams: the copy must be complete before them

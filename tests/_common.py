@@ -1,4 +1,22 @@
-"""Shared helpers for the parity tests: tolerances and small seeded inputs."""
+"""Shared helpers for the parity tests: the tolerance contract and small seeded inputs.
+
+The tolerance contract (per query, relative to the FP64 oracle). kappa is the query's
+condition number, the weighted mean of a ||q - x_i||^2 over its terms (oracle.kde_log):
+an evaluation whose squared distances carry a relative error e has a relative error
+about kappa * e, whatever the arithmetic, so no fixed bar can hold for every kappa.
+
+* plain FP32 form: 1e-5 for every query with kappa <= KAPPA0_PLAIN = 40;
+* tensor-core form: 1e-4 for every query with kappa <= KAPPA0_TC = 400 (its error
+  estimate hands the queries it cannot carry to the plain FP32 form);
+* above those, the measured FP32 bound C_F32 * kappa * 2^-24 (C_F32 = 5 up to d = 128,
+  growing like sqrt(d / 128) beyond), which the tests assert and report.
+
+Where the numbers come from: the plain form sums each squared distance in FP32 chains of
+16 coordinates whose sums are then added; against the oracle its largest error over
+mixtures with d = 16 ... 128 and kappa up to 220 measured 1.8 - 3.2 kappa 2^-24 (an
+emulation of the same arithmetic agrees), so 40 * 3.2 * 2^-24 = 7.6e-6 < 1e-5 and
+C_F32 = 5 leaves a margin above the largest ratio seen.
+"""
 import math
 
 import numpy as np
@@ -6,18 +24,27 @@ import numpy as np
 from paper_2407_07096_gb300 import datagen as G
 
 EPS32 = 2.0 ** -24
+KAPPA0_PLAIN = 40.0
+KAPPA0_TC = 400.0
+
+
+def c_f32(d):
+    """Measured-bound constant of the plain FP32 form at dimension d."""
+    return 5.0 * max(1.0, math.sqrt(d / 128.0))
 
 
 def tol_f32(kappa, d, base=1e-5):
-    """Per-query tolerance of the plain FP32 form.
+    """Per-query tolerance of the plain FP32 form: 1e-5 up to KAPPA0_PLAIN, the measured
+    FP32 bound above it."""
+    k = np.asarray(kappa, dtype=np.float64)
+    return np.where(k <= KAPPA0_PLAIN, base, np.maximum(base, c_f32(d) * k * EPS32))
 
-    The inputs are exact; each squared distance is summed in FP32 from d exact-to-FP32
-    squared differences, so its relative error is about sqrt(d) 2^-24 (random rounding)
-    and the term's relative error is that times a d^2 = the condition number kappa of
-    the dominant terms. The tolerance is the stated 1e-5, widened to 4 sqrt(d) kappa 2^-24
-    only for the ill-conditioned queries where FP32 cannot reach it (kappa sqrt(d) > ~40).
-    """
-    return np.maximum(base, 4.0 * math.sqrt(d) * np.asarray(kappa) * EPS32)
+
+def tol_tc(kappa, d, base=1e-4):
+    """Per-query tolerance of the tensor-core form: 1e-4 up to KAPPA0_TC, the plain form's
+    measured FP32 bound above it (those queries are recomputed in FP32)."""
+    k = np.asarray(kappa, dtype=np.float64)
+    return np.where(k <= KAPPA0_TC, base, np.maximum(base, c_f32(d) * k * EPS32))
 
 
 def mixture_inputs(seed, n, m, d, k=5, spread=3.0, std=1.0, dtype=np.float32):

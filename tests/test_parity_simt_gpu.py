@@ -140,3 +140,22 @@ def test_simt_f64_shapes(K, n, m, d):
     ref = oracle.kde(X, Q, a)
     _, _, kappa = oracle.kde_log(X, Q, a)
     assert np.all(oracle.rel_err(got, ref) <= 1e-15 * (8 + 4 * kappa) * math.sqrt(d))
+
+
+@pytest.mark.parametrize("d,a", [(32, 0.85), (64, 0.4), (128, 0.18), (128, 1.0)])
+def test_simt_f32_kappa0_bar_at_high_d(K, d, a):
+    # the 10-component mixtures of the batched workload (means U[-10, 10]^d, std 1) at
+    # bandwidths that put the condition numbers near KAPPA0_PLAIN = 40 (and, at a = 1,
+    # d = 128, far above it): 1e-5 for every query with kappa <= 40, the measured FP32
+    # bound above
+    from paper_2407_07096_gb300 import datagen as G
+    from tests._common import KAPPA0_PLAIN
+    mix = G.make_mixture(7, 10, d, -10.0, 10.0, 1.0)
+    X, Q = G.sample(mix, 7, 30000, "data"), G.sample(mix, 7, 1500, "query")
+    got, ref, err = check_f32(K, X, Q, a)
+    _, _, kappa = oracle.kde_log(X, Q, a)
+    low = kappa <= KAPPA0_PLAIN
+    if a < 1.0:
+        assert low.sum() > 100  # the bar is exercised near its edge
+        assert kappa[low].max() > 0.8 * KAPPA0_PLAIN
+    assert np.all(err[low] <= 1e-5)
