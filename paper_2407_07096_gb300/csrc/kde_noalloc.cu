@@ -35,7 +35,8 @@ constexpr int64_t kNoallocScratchBytes = 8ll << 20;  // 8 MiB
 constexpr int64_t kEntryBytes = sizeof(double) + sizeof(float);
 constexpr int64_t kNoallocMaxEntries = kNoallocScratchBytes / kEntryBytes;
 
-// Partials: doubles first, then floats (the float block starts at a 256-byte boundary).
+// Partials: splits*m doubles, then splits*m floats packed right behind them (8-byte
+// aligned), so splits*m <= 8 MiB / 12 bytes = 699050 entries always fit.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -121,18 +122,31 @@ kde_noalloc_kernel(const float *__restrict__ X, int64_t n, const float *__restri
             }
             __syncthreads();
             const int klen = (int)min((int64_t)KC, d - k0);
-            for (int k = 0; k < klen; ++k) {
-                const float4 qv = *reinterpret_cast<const float4 *>(&sQ[k * T + ty * 4]);
-                const float4 xv = *reinterpret_cast<const float4 *>(&sX[k * T + tx * 4]);
-                const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-                const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+            // chains of 16 coordinates, block sums added (the plain form's order)
+            for (int kb = 0; kb < klen; kb += 16) {
+                const int ke = min(klen, kb + 16);
+                float b2[4][4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float df = qa[i] - xa[j];
-                        d2[i][j] = fmaf(df, df, d2[i][j]);
-                    }
+                    for (int j = 0; j < 4; ++j) b2[i][j] = 0.f;
+                for (int k = kb; k < ke; ++k) {
+                    const float4 qv = *reinterpret_cast<const float4 *>(&sQ[k * T + ty * 4]);
+                    const float4 xv = *reinterpret_cast<const float4 *>(&sX[k * T + tx * 4]);
+                    const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+                    const float xa[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float df = qa[i] - xa[j];
+                            b2[i][j] = fmaf(df, df, b2[i][j]);
+                        }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) d2[i][j] += b2[i][j];
             }
         }
         const int64_t col0 = t * T + tx * 4;
@@ -225,11 +239,10 @@ extern "C" int stag_kde_eval_noalloc(const float *dX, int64_t n, const float *dQ
     splits = ceil_div(n_tiles, tps);
     if (q_tiles > 0x7fffffff) return fail(STAG_KDE_EINVAL, "m too large");
 
+    // splits * m <= kNoallocMaxEntries by construction: the packed layout fits exactly
     double *psum = reinterpret_cast<double *>(base);
-    const int64_t sum_bytes = round_up(splits * m * (int64_t)sizeof(double), 256);
-    float *pshift = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(base) + sum_bytes);
-    if (sum_bytes + splits * m * (int64_t)sizeof(float) > kNoallocScratchBytes)
-        return fail(STAG_KDE_EINVAL, "no-alloc scratch capacity exceeded");
+    float *pshift = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(base) +
+                                              splits * m * (int64_t)sizeof(double));
 
     cudaStream_t s = (cudaStream_t)stream;
     const float negc = (float)(-a * 1.4426950408889634);
