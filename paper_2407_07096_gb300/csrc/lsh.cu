@@ -8,10 +8,15 @@
 // equal those of any implementation that takes the decision the same way.
 //
 // Tables: for table l, point i's K values (functions l*K .. l*K+K-1) are mixed into a
-// 58-bit key; (l << 58 | key, i) pairs of all tables are sorted together by one stable
-// radix sort, so table l is the contiguous, key-sorted range [l*n, (l+1)*n) and each
-// bucket a run of equal keys with its point indices in increasing order. Two different
-// K-tuples mapping to the same 58-bit key would merge buckets (probability ~n^2 2^-59).
+// 58-bit key (a salted hash); (l << 58 | key, i) pairs of all tables are sorted together
+// by one stable radix sort, so table l is the contiguous, key-sorted range
+// [l*n, (l+1)*n) and each bucket a run of equal keys with its point indices in
+// increasing order. Membership is exact, not probabilistic: after the sort every pair
+// of neighbours with equal keys is checked to have equal K-tuples, and if two different
+// tuples share a key the keys are rebuilt with another salt (a run therefore always
+// holds one tuple); a query's lookup then recomputes the K values of the first point of
+// the run it found and keeps the run only if they equal the query's own (Sec. 2: a
+// collision needs all K values equal).
 //
 // Query: hash the queries, binary-search each table for the query's key (one thread per
 // (query, table)), then remove repeats across tables so that every query gets its
@@ -22,6 +27,7 @@
 // (one warp per query) and repeats are removed by a radix sort of (query << 32 | index)
 // keys and a per-query unique pass.
 #include <stdint.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <new>
@@ -37,6 +43,9 @@ struct stag_lsh {
     float *A = nullptr, *B = nullptr;  // functions: L*K x d, L*K
     uint64_t *keys = nullptr;          // n*L sorted keys (table id in bits 58..63)
     uint32_t *ids = nullptr;           // n*L point indices in key order
+    float *X = nullptr;                // n x d points (the lookup recomputes a member's K values)
+    uint64_t salt = 0;                 // salt of the bucket keys
+    int key_bits = 58;                 // bits of a bucket key
     // query scratch (grown on demand)
     void *scratch = nullptr;
     int64_t scratch_cap = 0;
@@ -57,7 +66,14 @@ constexpr int kHashRows = 8;   // rows per block
 constexpr int kKeyShift = 58;  // table id above the 58-bit bucket key
 
 // h = floor((<x, a> + b) / 4) in FP32, fixed order, saturated to int32 (the conversion
-// with rounding toward -inf saturates).
+// with rounding toward -inf saturates). One function of one row, the same operations as
+// the tiled kernel below.
+__device__ __forceinline__ int32_t hash_one(const float *__restrict__ x, const float *__restrict__ a, float b, int d) {
+    float s = 0.f;
+    for (int k = 0; k < d; ++k) s = __fmaf_rn(x[k], a[k], s);
+    return __float2int_rd(__fmul_rn(__fadd_rn(s, b), 0.25f));
+}
+
 __global__ void __launch_bounds__(kHashFns * kHashRows)
 lsh_hash_kernel(const float *__restrict__ X, int64_t n, int d, const float *__restrict__ A,
                 const float *__restrict__ B, int nf, int32_t *__restrict__ H) {
@@ -79,25 +95,45 @@ lsh_hash_kernel(const float *__restrict__ X, int64_t n, int d, const float *__re
     H[i * nf + f0 + lane] = __float2int_rd(v);
 }
 
-// 58-bit key of K hash values (a SplitMix64-style mix of each value into the state).
-__device__ __forceinline__ uint64_t bucket_key(const int32_t *h, int K) {
-    uint64_t z = 0x9E3779B97F4A7C15ull;
+// key_bits-bit key (at most 58) of K hash values: a SplitMix64-style mix of each value
+// into a salted state.
+__device__ __forceinline__ uint64_t bucket_key(const int32_t *h, int K, uint64_t salt, int key_bits) {
+    uint64_t z = 0x9E3779B97F4A7C15ull ^ salt;
     for (int k = 0; k < K; ++k) {
         z ^= (uint64_t)(uint32_t)h[k] + 0x9E3779B97F4A7C15ull + (z << 6) + (z >> 2);
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         z ^= z >> 31;
     }
-    return z >> (64 - kKeyShift);
+    return z >> (64 - key_bits);
 }
 
-__global__ void lsh_keys_kernel(const int32_t *__restrict__ H, int64_t n, int K, int L, uint64_t *__restrict__ keys,
-                                uint32_t *__restrict__ ids) {
+__global__ void lsh_keys_kernel(const int32_t *__restrict__ H, int64_t n, int K, int L, uint64_t salt, int key_bits,
+                                uint64_t *__restrict__ keys, uint32_t *__restrict__ ids) {
     const int64_t total = n * L;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = e / n, i = e % n;
-        keys[e] = ((uint64_t)l << kKeyShift) | bucket_key(H + i * (int64_t)K * L + l * K, K);
+        keys[e] = ((uint64_t)l << kKeyShift) | bucket_key(H + i * (int64_t)K * L + l * K, K, salt, key_bits);
         ids[e] = (uint32_t)i;
+    }
+}
+
+// After the sort: flags (*bad = 1) a pair of neighbours in one table whose keys are
+// equal but whose K-tuples differ (two buckets merged by the key).
+__global__ void lsh_collision_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ ids,
+                                     const int32_t *__restrict__ H, int64_t n, int K, int L, int *__restrict__ bad) {
+    const int64_t total = n * L;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x + 1; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (keys[e] != keys[e - 1]) continue;  // (the table id is part of the key)
+        const int64_t l = (int64_t)(keys[e] >> kKeyShift);
+        const int32_t *a = H + (int64_t)ids[e] * K * L + l * K;
+        const int32_t *b = H + (int64_t)ids[e - 1] * K * L + l * K;
+        for (int k = 0; k < K; ++k)
+            if (a[k] != b[k]) {
+                *bad = 1;
+                break;
+            }
     }
 }
 
@@ -112,16 +148,39 @@ __device__ __forceinline__ int64_t lower_bound(const uint64_t *a, int64_t lo, in
     return lo;
 }
 
-// Per (query, table): the bucket's range in the sorted arrays; per query: the total.
-__global__ void lsh_lookup_kernel(const int32_t *__restrict__ HQ, int64_t m, int K, int L,
-                                  const uint64_t *__restrict__ keys, int64_t n, int64_t *__restrict__ range,
+// The table view the lookup needs.
+struct LshTables {
+    const uint64_t *keys;
+    const uint32_t *ids;
+    const float *X, *A, *B;  // points and functions (L*K x d), offsets
+    int64_t n;
+    int d, K, L, key_bits;
+    uint64_t salt;
+};
+
+// Per (query, table): the bucket's range in the sorted arrays (empty unless the first
+// member's K values equal the query's: exact membership); per query: the total.
+__global__ void lsh_lookup_kernel(const int32_t *__restrict__ HQ, int64_t m, LshTables t, int64_t *__restrict__ range,
                                   unsigned long long *__restrict__ count) {
+    const int K = t.K, L = t.L;
+    const int64_t n = t.n;
     const int64_t total = m * L;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = e / L, l = e % L;
-        const uint64_t key = ((uint64_t)l << kKeyShift) | bucket_key(HQ + j * (int64_t)K * L + l * K, K);
-        const int64_t lo = lower_bound(keys, l * n, (l + 1) * n, key);
-        const int64_t hi = lower_bound(keys, lo, (l + 1) * n, key + 1);
+        const int32_t *hq = HQ + j * (int64_t)K * L + l * K;
+        const uint64_t key = ((uint64_t)l << kKeyShift) | bucket_key(hq, K, t.salt, t.key_bits);
+        const int64_t lo = lower_bound(t.keys, l * n, (l + 1) * n, key);
+        int64_t hi = lower_bound(t.keys, lo, (l + 1) * n, key + 1);
+        if (hi > lo) {
+            const float *x = t.X + (int64_t)t.ids[lo] * t.d;
+            for (int k = 0; k < K; ++k) {
+                const int64_t f = l * K + k;
+                if (hash_one(x, t.A + f * t.d, t.B[f], t.d) != hq[k]) {
+                    hi = lo;  // another tuple with the same key: not this query's bucket
+                    break;
+                }
+            }
+        }
         range[2 * e] = lo;
         range[2 * e + 1] = hi;
         if (count && hi > lo) atomicAdd(&count[j], (unsigned long long)(hi - lo));
@@ -313,7 +372,7 @@ int grow(void **p, int64_t *cap, int64_t bytes) {
     cudaFree(*p);
     *p = nullptr;
     *cap = 0;
-    STAG_CUDA_TRY(cudaMalloc(p, bytes));
+    STAG_CUDA_TRY(dev_malloc(p, bytes));
     *cap = bytes;
     return 0;
 }
@@ -346,6 +405,10 @@ int bits_for(int64_t v) {
     int b = 0;
     while (b < 63 && ((int64_t)1 << b) <= v) ++b;
     return b;
+}
+
+LshTables tables_of(const stag_lsh *h) {
+    return LshTables{h->keys, h->ids, h->X, h->A, h->B, h->n, (int)h->d, h->K, h->L, h->key_bits, h->salt};
 }
 
 // The bitmap path of lsh_run: bucket ranges, distinct counts per (query, slice), their
@@ -382,7 +445,7 @@ int lsh_run_bitmap(stag_lsh *h, const int32_t *HQ, int64_t *range, int64_t m, in
     STAG_CUDA_TRY(cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, h->device));
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)dev_sms * 2));
     count_launch(4);
-    lsh_lookup_kernel<<<grid_for_elems(m * h->L, 256), 256, 0, s>>>(HQ, m, h->K, h->L, h->keys, h->n, range, nullptr);
+    lsh_lookup_kernel<<<grid_for_elems(m * h->L, 256), 256, 0, s>>>(HQ, m, tables_of(h), range, nullptr);
     count_k<<<grid, kBmThreads, smem, s>>>(range, m, h->L, h->ids, words, slices, sw, ucount, nullptr, nullptr);
     scan_i64_kernel<<<1, 1024, 0, s>>>(ucount, items, item_off);
     lsh_item_to_query_off_kernel<<<grid_for_elems(m + 1, 256), 256, 0, s>>>(item_off, m, slices, dOff);
@@ -421,7 +484,7 @@ int lsh_run(stag_lsh *h, const float *dQ, int64_t m, int64_t *dOff, cudaStream_t
     if (bitmap_fits(h->n)) return lsh_run_bitmap(h, HQ, range, m, dOff, s, total);
     STAG_CUDA_TRY(cudaMemsetAsync(count, 0, m * 8, s));
     count_launch(2);
-    lsh_lookup_kernel<<<grid_for_elems(m * L, 256), 256, 0, s>>>(HQ, m, K, L, h->keys, h->n, range, count);
+    lsh_lookup_kernel<<<grid_for_elems(m * L, 256), 256, 0, s>>>(HQ, m, tables_of(h), range, count);
     scan_i64_kernel<<<1, 1024, 0, s>>>(count, m, raw_off);
     STAG_CUDA_TRY(cudaGetLastError());
     int64_t R = 0;
@@ -493,6 +556,7 @@ void free_lsh(stag_lsh *h) {
     cudaFree(h->B);
     cudaFree(h->keys);
     cudaFree(h->ids);
+    cudaFree(h->X);
     cudaFree(h->scratch);
     cudaFree(h->cand);
     cudaFree(h->sort_buf);
@@ -542,23 +606,28 @@ stag_lsh_t *stag_lsh_create(const float *X, int64_t n, int64_t d, int K, int L, 
     if (!g.ok) return (cuda_fail(cudaErrorInvalidDevice, "cudaSetDevice"), bail(0));
     if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return (cuda_fail(e, "cudaStreamCreate"), bail(0));
-    float *dX = nullptr;
     int32_t *H = nullptr;
     void *sortb = nullptr;
+    int *dbad = nullptr;
     auto cleanup = [&]() {
         cudaStreamSynchronize(h->stream);
-        cudaFree(dX);
         cudaFree(H);
         cudaFree(sortb);
+        cudaFree(dbad);
     };
     const int64_t nl = n * L;
-    if ((e = cudaMalloc(&h->A, nf * d * 4)) != cudaSuccess || (e = cudaMalloc(&h->B, nf * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&h->keys, nl * 8)) != cudaSuccess || (e = cudaMalloc(&h->ids, nl * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&dX, n * d * 4)) != cudaSuccess || (e = cudaMalloc(&H, n * nf * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&sortb, nl * 12 + radix_sort_hist_entries(nl) * 4)) != cudaSuccess) {
+    if ((e = dev_malloc(&h->A, nf * d * 4)) != cudaSuccess || (e = dev_malloc(&h->B, nf * 4)) != cudaSuccess ||
+        (e = dev_malloc(&h->keys, nl * 8)) != cudaSuccess || (e = dev_malloc(&h->ids, nl * 4)) != cudaSuccess ||
+        (e = dev_malloc(&h->X, n * d * 4)) != cudaSuccess || (e = dev_malloc(&H, n * nf * 4)) != cudaSuccess ||
+        (e = dev_malloc(&sortb, nl * 12 + radix_sort_hist_entries(nl) * 4)) != cudaSuccess ||
+        (e = dev_malloc(&dbad, sizeof(int))) != cudaSuccess) {
         cleanup();
         return (cuda_fail(e, "cudaMalloc (LSH tables)"), bail(0));
     }
+    float *dX = h->X;
+    // test hook: fewer key bits make different tuples share keys, exercising the salt
+    // retry and the lookup's tuple check
+    if (const char *kb = getenv("STAG_KDE_LSH_KEY_BITS")) h->key_bits = std::min(58, std::max(8, atoi(kb)));
     cudaStream_t s = h->stream;
     if ((e = cudaMemcpyAsync(h->A, A, nf * d * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(h->B, B, nf * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
@@ -567,14 +636,32 @@ stag_lsh_t *stag_lsh_create(const float *X, int64_t n, int64_t d, int K, int L, 
         return (cuda_fail(e, "cudaMemcpy (LSH inputs)"), bail(0));
     }
     int rc = launch_hash(h, dX, n, H, s);
-    if (!rc) {
-        count_launch();
-        lsh_keys_kernel<<<grid_for_elems(nl, 256), 256, 0, s>>>(H, n, K, L, h->keys, h->ids);
+    // keys, sort, and the check that no key is shared by two different K-tuples; on a
+    // shared key the tables are rebuilt with the next salt
+    constexpr int kSalts = 16;
+    bool clean = false;
+    for (int attempt = 0; attempt < kSalts && !rc && !clean; ++attempt) {
+        h->salt = 0xD1B54A32D192ED03ull * (uint64_t)attempt;
+        count_launch(2);
+        lsh_keys_kernel<<<grid_for_elems(nl, 256), 256, 0, s>>>(H, n, K, L, h->salt, h->key_bits, h->keys, h->ids);
         char *sb = (char *)sortb;
         rc = radix_sort_pairs(h->keys, h->ids, (uint64_t *)sb, (uint32_t *)(sb + nl * 8), (uint32_t *)(sb + nl * 12),
                               nl, 64, s);
+        if (rc) break;
+        int bad = 0;
+        if ((e = cudaMemsetAsync(dbad, 0, sizeof(int), s)) != cudaSuccess) {
+            rc = cuda_fail(e, "cudaMemsetAsync");
+            break;
+        }
+        lsh_collision_kernel<<<grid_for_elems(nl, 256), 256, 0, s>>>(h->keys, h->ids, H, n, K, L, dbad);
+        if ((e = cudaMemcpyAsync(&bad, dbad, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+            rc = cuda_fail(e, "LSH table build");
+            break;
+        }
+        clean = bad == 0;
     }
-    if (!rc && (e = cudaStreamSynchronize(s)) != cudaSuccess) rc = cuda_fail(e, "LSH table build");
+    if (!rc && !clean) rc = fail(STAG_KDE_EUNSUPPORTED, "LSH tables: every salt left two K-tuples sharing a key");
     cleanup();
     if (rc) return bail(rc);
     return h;

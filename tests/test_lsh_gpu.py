@@ -170,3 +170,32 @@ def test_paper_parameters_sampled():
     want = _lists(woff, widx)
     for r, w in zip(rows, want):
         assert got[r] == w
+
+
+def test_membership_is_exact_when_keys_collide(monkeypatch):
+    # With 12-bit bucket keys (a test hook; the library uses 58 bits) many different
+    # K-tuples share a key: the build must pick a salt under which no two tuples of the
+    # points share a key, and each lookup must reject a run whose tuple differs from the
+    # query's. Tight data (few tuples per table) and far queries (new tuples only):
+    # hundreds of lookups land on another tuple's key, and the lists must still equal
+    # the oracle's, which compares tuples.
+    E = _cls()
+    rng = np.random.default_rng(5)
+    X = (0.3 * rng.normal(size=(3000, 8))).astype(np.float32)
+    near = (0.3 * rng.normal(size=(2000, 8))).astype(np.float32)
+    far = rng.uniform(-200, 200, size=(20000, 8)).astype(np.float32)
+    Q = np.concatenate([near, far])
+    monkeypatch.setenv("STAG_KDE_LSH_KEY_BITS", "12")
+    with E(X, 3, 8, seed=11) as lsh:
+        off, idx = lsh.query(Q)
+        A, B = lsh.A, lsh.B
+    monkeypatch.delenv("STAG_KDE_LSH_KEY_BITS")
+    HX, HQ = oracle.lsh_hash(X, A, B), oracle.lsh_hash(Q, A, B)
+    woff, widx = oracle.lsh_candidates(HX, HQ, 3, 8)
+    assert np.array_equal(off, woff)
+    assert np.array_equal(idx, widx)
+    assert off[len(near)] > 0  # the near queries found their buckets
+    # the far queries' tuples are new: count the lookups whose 12-bit key space alone
+    # would have matched a bucket (distinct tuples per table vs 4096 keys)
+    tuples = sum(len({tuple(r) for r in HX[:, l * 3:(l + 1) * 3]}) for l in range(8))
+    assert tuples * len(far) / 4096 > 100
