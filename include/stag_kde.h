@@ -42,7 +42,7 @@ extern "C" {
 
 #define STAG_KDE_OK 0
 #define STAG_KDE_EINVAL (-1)     /* bad argument (sizes, NULL pointer, non-finite value)  */
-#define STAG_KDE_ENOMEM (-2)     /* device or host allocation failed                       */
+#define STAG_KDE_ENOMEM (-2)     /* device or host allocation failed (also: admission)     */
 #define STAG_KDE_ECUDA (-3)      /* a CUDA call failed (message has the CUDA error string) */
 #define STAG_KDE_ETIMEDOUT (-4)  /* a bounded wait expired                                 */
 #define STAG_KDE_ECANCELED (-5)  /* request cancelled or server stopped                    */
@@ -95,8 +95,9 @@ void stag_kde_opts_init(stag_kde_opts *o);
  * Device memory held for the point set: the plain form's tiled copy (about n * d_pad * 4
  * bytes, d_pad = d rounded up to 4); the tensor-core form adds the FP16 splits of the
  * points (about n * (2 * Kp + 16) * 2 bytes, Kp = d rounded up to 16, 32, 64 or 128),
- * per-tile centres and radii, and a k-d ordered FP32 copy (n * d * 4 bytes) from which
- * flagged queries are recomputed. Per-query scratch comes on top (stag_kde_reserve).
+ * per-tile centres and radii, and for d <= 16 a k-d ordered FP32 copy (n * d * 4 bytes)
+ * from which flagged queries are recomputed. Per-query scratch comes on top
+ * (stag_kde_reserve).
  * Returns NULL on error (see stag_kde_last_error()).
  */
 stag_kde_t *stag_kde_create(const float *X, int64_t n, int64_t d, double a);
@@ -258,6 +259,18 @@ int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *d
  * Synchronises with the device. */
 int stag_kde_last_recomputed(stag_kde_t *h, int64_t *count);
 
+/*
+ * Limit, in nanoseconds, of each bounded wait inside the tensor-core kernel (its warps
+ * hand shared-memory stages and TMEM accumulators to one another through mbarriers;
+ * every wait on one gives up after this long). On expiry the kernel records an error,
+ * makes its other warps stop, waits (again bounded) for its own copies and MMAs in
+ * flight, frees its TMEM and returns; the call that synchronises on the result reports
+ * STAG_KDE_ETIMEDOUT and the handle stays usable. 0 restores the default of 2 s; the
+ * limit must not exceed 60 s. A watchdog for deployments, and the way tests make a wait
+ * expire without faulting the GPU. No effect on the other forms.
+ */
+int stag_kde_set_wait_limit(stag_kde_t *h, int64_t limit_ns);
+
 /* Releases the handle and its device memory. NULL-safe. */
 void stag_kde_destroy(stag_kde_t *h);
 
@@ -281,6 +294,16 @@ const char *stag_kde_version(void);
  */
 int stag_kde_profile_begin(stag_kde_t *h);
 int stag_kde_profile_end(stag_kde_t *h, double *ms, int64_t *launches, double *pairs);
+
+/*
+ * Measures the ex2.approx throughput of the current device (the MUFU unit that bounds
+ * the Gaussian kernel's epilogue: one ex2 per query-point pair): 8 independent chains
+ * of `iters` steps per thread, 8 blocks of 256 threads per SM, timed with CUDA events
+ * after a warm-up launch. Writes the kernel time (ms) and the ex2 results per second.
+ * Synchronises the device; 1 <= iters <= 2^24. Not part of the paper's method: it is the
+ * measured peak the benchmark reports the kernels' fraction of roofline against.
+ */
+int stag_kde_probe_ex2(int64_t iters, double *ms, double *ex2_per_s);
 
 /* Number of CUDA kernels this library has launched in this process (all handles,
  * all threads). Lets a caller count the device work behind a sequence of calls. */

@@ -49,6 +49,8 @@ SIGNATURES = [
     ("stag_kde_create_ex", _VP, [_VP, _INT, _I64, _I64, _DBL, ctypes.POINTER(Opts)]),
     ("stag_kde_query", _INT, [_VP, _VP, _I64, _VP]),
     ("stag_kde_query_dev", _INT, [_VP, _VP, _I64, _VP, _VP]),
+    ("stag_kde_set_wait_limit", _INT, [_VP, _I64]),
+    ("stag_kde_probe_ex2", _INT, [_I64, _VP, _VP]),
     ("stag_kde_query_subset", _INT, [_VP, _VP, _I64, _VP, _VP, _VP, _VP]),
     ("stag_kde_query_subset_dev", _INT, [_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP]),
     ("stag_lsh_create", _VP, [_VP, _I64, _I64, _INT, _INT, _VP, _VP, _INT]),

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,18 @@ int cuda_fail(cudaError_t e, const char *what);
 // ---------------------------------------------------------------------------------
 constexpr int kSimtTile = 64;  // rows per tile (queries per block, points per tile)
 constexpr int kSimtKC = 32;    // coordinates per shared-memory chunk
+
+// Every device allocation of the library goes through dev_malloc. It is also the
+// library's host-side fault-injection point: while the environment variable
+// STAG_KDE_INJECT_ALLOC_FAIL holds a positive integer k, the k-th device allocation
+// counted from the moment the variable took that value fails as cudaErrorMemoryAllocation
+// (reported as STAG_KDE_ENOMEM), so tests can fail each allocation of a call in turn
+// without exhausting the GPU.
+cudaError_t dev_malloc_bytes(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc_bytes(reinterpret_cast<void **>(p), bytes);
+}
 
 // Process-wide count of kernel launches (reported by stag_kde_launch_count).
 void count_launch(int k = 1);
@@ -64,6 +77,7 @@ struct stag_kde {
     bool is_view = false;          // shares another handle's point-set data (serving slots)
     int tune_eg = 0;               // tensor-core epilogue warp groups (0 = default)
     int tune_tiles_per_unit = 0;   // point tiles per work unit (0 = heuristic)
+    uint64_t wait_ns = 2000000000ull;  // limit of each bounded device wait (stag_kde_set_wait_limit)
     cudaStream_t stream = nullptr;  // the handle's own stream (host API)
 
     // plain FP32 form: tile-transposed points
@@ -173,7 +187,7 @@ int tc_prep_public(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s);
 int64_t tc_fill_inst(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t unit_begin, void *inst,
                      int64_t *splits);
 int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total_units, int *err, int sm_count,
-                    cudaStream_t s);
+                    uint64_t wait_ns, cudaStream_t s);
 int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s);
 // kde_batch.cu
 void batch_forget_handle(stag_kde *h);

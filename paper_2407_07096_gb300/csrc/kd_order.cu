@@ -305,12 +305,12 @@ int kd_reorder(const float *dX, int64_t n, int64_t d, int BN, float *dXs, cudaSt
         cudaFree(dim);
     };
     cudaError_t e = cudaSuccess;
-    if ((e = cudaMalloc(&perm, n * 4)) || (e = cudaMalloc(&vtmp, n * 4)) || (e = cudaMalloc(&keys, n * 8)) ||
-        (e = cudaMalloc(&ktmp, n * 8)) || (e = cudaMalloc(&mn, max_seg * d * 4)) ||
-        (e = cudaMalloc(&mx, max_seg * d * 4)) || (e = cudaMalloc(&hist, radix_sort_hist_entries(n) * 4)) ||
-        (e = cudaMalloc(&dim, max_seg * sizeof(int)))) {
+    if ((e = dev_malloc(&perm, n * 4)) || (e = dev_malloc(&vtmp, n * 4)) || (e = dev_malloc(&keys, n * 8)) ||
+        (e = dev_malloc(&ktmp, n * 8)) || (e = dev_malloc(&mn, max_seg * d * 4)) ||
+        (e = dev_malloc(&mx, max_seg * d * 4)) || (e = dev_malloc(&hist, radix_sort_hist_entries(n) * 4)) ||
+        (e = dev_malloc(&dim, max_seg * sizeof(int)))) {
         cleanup();
-        return cuda_fail(e, "cudaMalloc(k-d ordering)");
+        return cuda_fail(e, "dev_malloc(k-d ordering)");
     }
     count_launch();
     kd_init_kernel<<<grid_of(n, 256), 256, 0, s>>>(perm, n);

@@ -52,6 +52,7 @@ struct BatchPlan {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t launches_per_run = 0;
+    uint64_t wait_ns = 0;  // the longest wait limit of the batch's handles
 };
 
 std::mutex g_mu;
@@ -117,7 +118,7 @@ int build_tables(BatchPlan *p) {
             ++cl.n_inst;
         }
         if (!cl.n_inst) continue;
-        STAG_CUDA_TRY(cudaMalloc(&cl.d_table, host.size()));
+        STAG_CUDA_TRY(dev_malloc(&cl.d_table, host.size()));
         STAG_CUDA_TRY(cudaMemcpy(cl.d_table, host.data(), host.size(), cudaMemcpyHostToDevice));
         p->classes.push_back(cl);
     }
@@ -134,7 +135,8 @@ int enqueue(BatchPlan *p, cudaStream_t s) {
     }
     for (auto &c : p->classes) {
         if (rc) break;
-        rc = tc_launch_table(c.Kp, p->eg, c.d_table, c.n_inst, c.total_units, p->d_err, p->hs[0]->sm_count, s);
+        rc = tc_launch_table(c.Kp, p->eg, c.d_table, c.n_inst, c.total_units, p->d_err, p->hs[0]->sm_count,
+                             p->wait_ns, s);
     }
     for (size_t i = 0; i < p->hs.size() && !rc; ++i) {
         stag_kde *h = p->hs[i];
@@ -199,7 +201,7 @@ int build_plan(BatchPlan *p) {
     // let every earlier piece of work on the device finish first
     STAG_CUDA_TRY(cudaDeviceSynchronize());
     STAG_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
-    STAG_CUDA_TRY(cudaMalloc(&p->d_err, sizeof(int)));
+    STAG_CUDA_TRY(dev_malloc(&p->d_err, sizeof(int)));
     STAG_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
     STAG_CUDA_TRY(cudaMallocHost(&p->h_err, sizeof(int)));
     *p->h_err = 0;
@@ -271,8 +273,8 @@ extern "C" int stag_kde_autotune(stag_kde_t *h, const void *dQ, int64_t m) {
     const int egs[] = {2, 4};
     const int tpus[] = {0, 16, 32, 64, 128};
     double *dout = nullptr;
-    cudaError_t e = cudaMalloc(&dout, m * sizeof(double));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(autotune)");
+    cudaError_t e = dev_malloc(&dout, m * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(e, "dev_malloc(autotune)");
     const uint64_t before = stag_kde_launch_count();
     const int keep_eg = h->tune_eg, keep_tpu = h->tune_tiles_per_unit;
     double best = 1e300;
@@ -361,6 +363,7 @@ extern "C" int stag_kde_query_batch(stag_kde_t *const *hs, const void *const *dQ
         plan->key = key;
         plan->device = device;
         for (int64_t i = 0; i < count; ++i) {
+            plan->wait_ns = std::max<uint64_t>(plan->wait_ns, hs[i]->wait_ns);
             plan->hs.push_back(hs[i]);
             plan->qs.push_back(dQs[i]);
             plan->ms.push_back(ms[i]);

@@ -267,8 +267,8 @@ stag_srv_t *stag_srv_start(const stag_srv_opts *o) {
         s.views.assign(srv->datasets.size(), nullptr);
         cudaError_t e;
         if ((e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaMalloc(&s.dq, qbytes)) != cudaSuccess ||
-            (e = cudaMalloc(&s.dout, srv->max_rows * 8)) != cudaSuccess ||
+            (e = dev_malloc(&s.dq, qbytes)) != cudaSuccess ||
+            (e = dev_malloc(&s.dout, srv->max_rows * 8)) != cudaSuccess ||
             (e = cudaMallocHost(&s.hq, qbytes)) != cudaSuccess ||
             (e = cudaMallocHost(&s.hout, srv->max_rows * 8)) != cudaSuccess) {
             cuda_fail(e, "server slot set-up");

@@ -71,10 +71,12 @@ struct TcData {
     __half *b_hi = nullptr, *b_lo = nullptr;  // [n_pad][Kp]
     __half *b_aug = nullptr;                  // [n_pad][16]: -g / (2 scale) in 3 FP16 pieces, then 0
     __half *a_aug = nullptr;                  // [128][16]: s_a, s_a, s_a, 0, ...
-    float *tinfo = nullptr;                   // [T][4]: tile RMS radius, 0, 0, 0
+    float *tinfo = nullptr;                   // [T][4]: RMS radius, max radius (rounded up to bound
+                                              //         FP32 distances), 0, 0
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
     float *cg = nullptr;                      // [Kp]: global centre c_g
     float *xs = nullptr;                      // [n][d]: the points in tile (k-d) order, FP32 row-major
+                                              //         (handles that recompute flagged queries)
     double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
     unsigned *vmax_bits = nullptr;            // max |x_k - c_t,k| (float bits)
     unsigned *xmax_bits = nullptr;            // max |x_k - c_g,k| (float bits)
@@ -100,7 +102,6 @@ struct TcData {
 
 namespace {
 
-constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
 constexpr int kErrTimeout = 1;
 constexpr int BM = 128;  // queries per tile (MMA M, TMEM lanes)
 // Queries whose estimated tensor-core error exceeds this are recomputed with the plain
@@ -279,7 +280,7 @@ __device__ __forceinline__ void epi_chunk(uint64_t &acc_a, uint64_t &acc_b, cons
 template <int KP, int BN, int SB, int SMETA, int AB, int EG>
 __global__ void __launch_bounds__(64 + 128 * EG, 1) __maxnreg__(EG >= 4 ? 112 : 200)
 kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ table, int n_inst,
-              int64_t total_units, int *err) {
+              int64_t total_units, int *err, uint64_t wait_ns, uint64_t stall_ns) {
     const TcInst *insts = table ? table : &inst0;
     using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
     using G = Geo<KP>;
@@ -357,14 +358,24 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             uint32_t ucount = 0, tcount = 0;
             uint32_t issued_a = 0, issued_b = 0, issued_m = 0;
             bool ok = true;
+            if (stall_ns) {
+                // injected delay (tests of the bounded waits): the consumers find nothing
+                // arriving for stall_ns; ends early once another role has given up
+                const uint64_t t0 = ptx::globaltimer();
+                while (ptx::globaltimer() - t0 < stall_ns && !*abort_flag) __nanosleep(1000);
+            }
             for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++ucount) {
+                if (*abort_flag) {  // another role gave up: issue nothing more
+                    ok = false;
+                    break;
+                }
                 const TcInst &I = *find_inst(insts, n_inst, u);
                 const int64_t lu = u - I.unit_begin;
                 const int64_t split = lu / I.q_tiles, qt = lu % I.q_tiles;
                 const int64_t t0 = split * I.tiles_per_split;
                 const int64_t t1 = min(I.T, t0 + I.tiles_per_split);
                 const int ab = ucount % AB;
-                if (!ptx::mbar_wait_bounded(&a_empty[ab], ((ucount / AB) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                if (!ptx::mbar_wait_bounded(&a_empty[ab], ((ucount / AB) & 1) ^ 1, wait_ns, abort_flag)) {
                     timed_out();
                     ok = false;
                     break;
@@ -381,7 +392,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 ++issued_a;
                 for (int64_t t = t0; t < t1; ++t, ++tcount) {
                     const int sb = tcount % SB;
-                    if (!ptx::mbar_wait_bounded(&empty_b[sb], ((tcount / SB) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                    if (!ptx::mbar_wait_bounded(&empty_b[sb], ((tcount / SB) & 1) ^ 1, wait_ns, abort_flag)) {
                         timed_out();
                         ok = false;
                         break;
@@ -397,7 +408,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                     ptx::tma_load_2d(bbuf + 2 * C::B_PLANE, &I.map_baug, 0, (int)(t * BN), &full_b[sb]);
                     ++issued_b;
                     const int ms = tcount % SMETA;
-                    if (!ptx::mbar_wait_bounded(&empty_m[ms], ((tcount / SMETA) & 1) ^ 1, kWaitLimitNs, abort_flag)) {
+                    if (!ptx::mbar_wait_bounded(&empty_m[ms], ((tcount / SMETA) & 1) ^ 1, wait_ns, abort_flag)) {
                         timed_out();
                         ok = false;
                         break;
@@ -437,7 +448,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 const int64_t t0 = split * I.tiles_per_split;
                 const int64_t t1 = min(I.T, t0 + I.tiles_per_split);
                 const int ab = ucount % AB;
-                if (!ptx::mbar_wait_bounded(&a_full[ab], (ucount / AB) & 1, kWaitLimitNs, abort_flag)) {
+                if (!ptx::mbar_wait_bounded(&a_full[ab], (ucount / AB) & 1, wait_ns, abort_flag)) {
                     timed_out();
                     ok = false;
                     break;
@@ -448,7 +459,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 const uint32_t alo_aug = ptx::smem_desc_lo(abase + 2 * C::A_PLANE, 16);
                 for (int64_t t = t0; t < t1 && ok; ++t, ++tcount) {
                     const int sb = tcount % SB;
-                    if (!ptx::mbar_wait_bounded(&full_b[sb], (tcount / SB) & 1, kWaitLimitNs, abort_flag)) {
+                    if (!ptx::mbar_wait_bounded(&full_b[sb], (tcount / SB) & 1, wait_ns, abort_flag)) {
                         timed_out();
                         ok = false;
                         break;
@@ -487,7 +498,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                         for (int h = 0; h < 2; ++h) {
                             const uint32_t k = 2 * tcount + h;  // half tile index, CTA-wide
                             const int acc = k % C::NACC;
-                            if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((k / C::NACC) & 1) ^ 1, kWaitLimitNs,
+                            if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((k / C::NACC) & 1) ^ 1, wait_ns,
                                                         abort_flag)) {
                                 timed_out();
                                 ok = false;
@@ -499,7 +510,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                         }
                     } else {
                         const int acc = tcount % C::NACC;
-                        if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((tcount / C::NACC) & 1) ^ 1, kWaitLimitNs,
+                        if (!ptx::mbar_wait_bounded(&acc_empty[acc], ((tcount / C::NACC) & 1) ^ 1, wait_ns,
                                                     abort_flag)) {
                             timed_out();
                             ok = false;
@@ -552,8 +563,8 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             // is broadcast so that the warp never splits around __syncwarp
             bool got = true;
             if (lane == 0)
-                got = ptx::mbar_wait_bounded(&acc_full[acc], (k / C::NACC) & 1, kWaitLimitNs, abort_flag) &&
-                      ptx::mbar_wait_bounded(&full_m[ms], (tc / SMETA) & 1, kWaitLimitNs, abort_flag);
+                got = ptx::mbar_wait_bounded(&acc_full[acc], (k / C::NACC) & 1, wait_ns, abort_flag) &&
+                      ptx::mbar_wait_bounded(&full_m[ms], (tc / SMETA) & 1, wait_ns, abort_flag);
             if (!__shfl_sync(0xffffffffu, (int)got, 0)) return false;
             ptx::tc_fence_after();
             const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
@@ -654,7 +665,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             // through shared memory; group 0 adds them in group order), then store the
             // unit's partials
             if (grp > 0) {
-                const bool got = ptx::mbar_wait_bounded(merge_empty, (ucount & 1) ^ 1, kWaitLimitNs, abort_flag);
+                const bool got = ptx::mbar_wait_bounded(merge_empty, (ucount & 1) ^ 1, wait_ns, abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
                     timed_out();
                     break;
@@ -665,7 +676,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(merge_full);
             } else {
-                const bool got = ptx::mbar_wait_bounded(merge_full, ucount & 1, kWaitLimitNs, abort_flag);
+                const bool got = ptx::mbar_wait_bounded(merge_full, ucount & 1, wait_ns, abort_flag);
                 if (!__all_sync(0xffffffffu, got)) {
                     timed_out();
                     break;
@@ -974,17 +985,17 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
 // (with a 1e-5 relative slack on sqrt(R_t) for rounding), so LB = max_t lb_t bounds the
 // row's largest term from below, and a tile with ub_t < LB - 64 holds only terms below
 // 2^-64 of it: all of them together change the sum by less than n 2^-64 relative, and
-// the tile is skipped. The others are evaluated like the plain FP32 form (direct
-// differences in FP32, one ex2 per pair, a per-lane power-of-two shift raised when a term
-// would pass 2^64, FP32 partial sums flushed to FP64 every 16 terms, merged in FP64 in a
-// fixed order). One block of 8 warps per flagged query (grid-stride over the device
-// count): tiles are bounded 32 at a time (one ballot), warp w takes every 8th included
-// tile of each group of 32, its lanes split the tile's points.
+// the tile is skipped. The others are evaluated like the plain FP32 form: squared
+// distances by direct differences in FP32 chains of 16 coordinates whose sums are added
+// (the plain form's order, so the same d2 bits), one ex2 per pair, a per-lane
+// power-of-two shift raised when a term would pass 2^64, FP32 partial sums flushed to
+// FP64 every 16 terms, merged in FP64 in a fixed order. One block of 8 warps per flagged
+// query (grid-stride over the device count): tiles are bounded 32 at a time (one
+// ballot), warp w takes every 8th included tile of each group of 32, its lanes take two
+// points each (packed FP32x2 arithmetic) until the tile is done.
 constexpr int kPrunedWarps = 8;
 constexpr float kPruneLog2 = 64.f;
-// Above this d the distances concentrate (few tiles drop out) and the plain kernel's
-// register-tiled form does the recompute faster.
-constexpr int64_t kPrunedMaxD = 16;
+constexpr int64_t kPrunedMaxD = 16;  // the per-query pruned pass serves d <= 16
 
 template <bool kVec4>
 __global__ void __launch_bounds__(32 * kPrunedWarps)
@@ -1008,6 +1019,29 @@ tc_fixup_pruned_kernel(const float *__restrict__ Q, int d, const int *__restrict
         ub = -g * g;
         lb = -h2 * h2;
     };
+    float shift = kShiftInit, acc32 = 0.f;
+    double acc64 = 0.0;
+    int nacc = 0;
+    auto add_term = [&](float d2) {
+        float e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
+        if (!(fabsf(e) <= kGuard)) {
+            // first term, or one far above the current shift: move the shift up
+            const float s_new = fmaxf(ceilf(negc * d2), kShiftInit);
+            if (s_new > shift) {
+                const int de = cexp(shift - s_new);
+                acc32 = ldexpf(acc32, de);
+                acc64 = ldexp(acc64, de);
+                shift = s_new;
+            }
+            e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
+        }
+        acc32 += e;
+        if (++nacc == 16) {
+            acc64 += (double)acc32;
+            acc32 = 0.f;
+            nacc = 0;
+        }
+    };
     for (int64_t w = blockIdx.x; w < cnt; w += gridDim.x) {
         const int64_t q = fix_idx[w];
         for (int k = threadIdx.x; k < d; k += 32 * kPrunedWarps) sq[k] = Q[q * d + k];
@@ -1026,9 +1060,10 @@ tc_fixup_pruned_kernel(const float *__restrict__ Q, int d, const int *__restrict
 #pragma unroll
         for (int i = 1; i < kPrunedWarps; ++i) thr = fmaxf(thr, wlb[i]);
         thr -= kPruneLog2;
-        float shift = kShiftInit, acc32 = 0.f;
-        double acc64 = 0.0;
-        int nacc = 0;
+        shift = kShiftInit;
+        acc32 = 0.f;
+        acc64 = 0.0;
+        nacc = 0;
         for (int64_t t0 = 0; t0 < T; t0 += 32) {
             bool keep = false;
             if (t0 + lane < T) {
@@ -1042,46 +1077,41 @@ tc_fixup_pruned_kernel(const float *__restrict__ Q, int d, const int *__restrict
                 mask &= mask - 1u;
                 if (rank % kPrunedWarps != warp) continue;
                 const int64_t p1 = min(n, (t + 1) * BN);
-                for (int64_t p = t * BN + lane; p < p1; p += 32) {
-                    const float *x = xs + p * d;
-                    float d2 = 0.f;
-                    if constexpr (kVec4) {
-                        for (int k = 0; k < d; k += 4) {
-                            const float4 xv = *reinterpret_cast<const float4 *>(x + k);
-                            const float4 qv = *reinterpret_cast<const float4 *>(sq + k);
-                            float e = qv.x - xv.x;
-                            d2 = fmaf(e, e, d2);
-                            e = qv.y - xv.y;
-                            d2 = fmaf(e, e, d2);
-                            e = qv.z - xv.z;
-                            d2 = fmaf(e, e, d2);
-                            e = qv.w - xv.w;
-                            d2 = fmaf(e, e, d2);
+                // two points per lane: p and p + 32 (the second repeats the first past the end)
+                for (int64_t p = t * BN + lane; p < p1; p += 64) {
+                    const bool two = p + 32 < p1;
+                    const float *xa = xs + p * d;
+                    const float *xb = xs + (two ? p + 32 : p) * d;
+                    uint64_t d2 = 0ull;  // {0.f, 0.f}
+                    for (int kb = 0; kb < d; kb += 16) {
+                        const int ke = min(d, kb + 16);
+                        uint64_t b2 = 0ull;
+                        if constexpr (kVec4) {
+                            for (int k = kb; k < ke; k += 4) {
+                                const float4 va = *reinterpret_cast<const float4 *>(xa + k);
+                                const float4 vb = *reinterpret_cast<const float4 *>(xb + k);
+                                const float4 qv = *reinterpret_cast<const float4 *>(sq + k);
+                                uint64_t df = f2::sub(f2::pack(qv.x, qv.x), f2::pack(va.x, vb.x));
+                                b2 = f2::fma(df, df, b2);
+                                df = f2::sub(f2::pack(qv.y, qv.y), f2::pack(va.y, vb.y));
+                                b2 = f2::fma(df, df, b2);
+                                df = f2::sub(f2::pack(qv.z, qv.z), f2::pack(va.z, vb.z));
+                                b2 = f2::fma(df, df, b2);
+                                df = f2::sub(f2::pack(qv.w, qv.w), f2::pack(va.w, vb.w));
+                                b2 = f2::fma(df, df, b2);
+                            }
+                        } else {
+                            for (int k = kb; k < ke; ++k) {
+                                const uint64_t df = f2::sub(f2::pack(sq[k], sq[k]), f2::pack(xa[k], xb[k]));
+                                b2 = f2::fma(df, df, b2);
+                            }
                         }
-                    } else {
-                        for (int k = 0; k < d; ++k) {
-                            const float e = sq[k] - x[k];
-                            d2 = fmaf(e, e, d2);
-                        }
+                        d2 = f2::add(d2, b2);
                     }
-                    float e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
-                    if (!(fabsf(e) <= kGuard)) {
-                        // first term, or one far above the current shift: move the shift up
-                        const float s_new = fmaxf(ceilf(negc * d2), kShiftInit);
-                        if (s_new > shift) {
-                            const int de = cexp(shift - s_new);
-                            acc32 = ldexpf(acc32, de);
-                            acc64 = ldexp(acc64, de);
-                            shift = s_new;
-                        }
-                        e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
-                    }
-                    acc32 += e;
-                    if (++nacc == 16) {
-                        acc64 += (double)acc32;
-                        acc32 = 0.f;
-                        nacc = 0;
-                    }
+                    float da, db;
+                    f2::unpack(d2, da, db);
+                    add_term(da);
+                    if (two) add_term(db);
                 }
             }
         }
@@ -1175,6 +1205,15 @@ int make_map(CUtensorMap *map, void *base, int64_t rows, int width, int box_rows
     return 0;
 }
 
+// Test hook: STAG_KDE_INJECT_PRODUCER_STALL_NS (at most 1 s) delays the start of the
+// tensor-core kernel's TMA producer, so that the other warps' bounded waits expire.
+uint64_t injected_stall_ns() {
+    const char *v = getenv("STAG_KDE_INJECT_PRODUCER_STALL_NS");
+    if (!v) return 0;
+    const long long ns = atoll(v);
+    return ns <= 0 ? 0 : (uint64_t)std::min(ns, 1000000000ll);
+}
+
 int kp_for(int64_t d) {
     if (d <= 16) return 16;
     if (d <= 32) return 32;
@@ -1189,7 +1228,8 @@ int grid_for(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_di
 
 template <int KP, int BN, int SB, int SMETA, int AB, int EG>
 int launch_tc(const TcInst &inst0, const TcInst *table, int n_inst, int64_t total_units, int *err, int sm_count,
-              cudaStream_t s) {
+              uint64_t wait_ns, cudaStream_t s) {
+    const uint64_t stall_ns = injected_stall_ns();
     using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
     auto kern = kde_tc_kernel<KP, BN, SB, SMETA, AB, EG>;
     static_assert(C::SMEM <= 232448, "shared memory budget");
@@ -1200,23 +1240,23 @@ int launch_tc(const TcInst &inst0, const TcInst *table, int n_inst, int64_t tota
     STAG_CUDA_TRY(attr);
     const int grid = (int)std::min<int64_t>(total_units, sm_count);
     count_launch();
-    kern<<<grid, C::THREADS, smem, s>>>(inst0, table, n_inst, total_units, err);
+    kern<<<grid, C::THREADS, smem, s>>>(inst0, table, n_inst, total_units, err, wait_ns, stall_ns);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }
 
 // Dispatch on the operand width and the number of epilogue warp groups.
 int launch_tc_any(int Kp, int eg, const TcInst &inst0, const TcInst *table, int n_inst, int64_t total_units,
-                  int *err, int sm_count, cudaStream_t s) {
+                  int *err, int sm_count, uint64_t wait_ns, cudaStream_t s) {
     switch (Kp * 10 + eg) {
-        case 162: return launch_tc<16, 256, 4, 8, 2, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 164: return launch_tc<16, 256, 4, 8, 2, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 322: return launch_tc<32, 256, 4, 8, 2, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 324: return launch_tc<32, 256, 4, 8, 2, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 642: return launch_tc<64, 256, 2, 8, 1, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 644: return launch_tc<64, 256, 2, 8, 1, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 1282: return launch_tc<128, 128, 2, 8, 1, 2>(inst0, table, n_inst, total_units, err, sm_count, s);
-        case 1284: return launch_tc<128, 128, 2, 8, 1, 4>(inst0, table, n_inst, total_units, err, sm_count, s);
+        case 162: return launch_tc<16, 256, 4, 8, 2, 2>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 164: return launch_tc<16, 256, 4, 8, 2, 4>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 322: return launch_tc<32, 256, 4, 8, 2, 2>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 324: return launch_tc<32, 256, 4, 8, 2, 4>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 642: return launch_tc<64, 256, 2, 8, 1, 2>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 644: return launch_tc<64, 256, 2, 8, 1, 4>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 1282: return launch_tc<128, 128, 2, 8, 1, 2>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
+        case 1284: return launch_tc<128, 128, 2, 8, 1, 4>(inst0, table, n_inst, total_units, err, sm_count, wait_ns, s);
     }
     return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported operand width");
 }
@@ -1289,7 +1329,7 @@ int tc_make_view(const stag_kde *base, stag_kde *view) {
     tc->map_blo = b->map_blo;
     tc->map_baug = b->map_baug;
     tc->map_aaug = b->map_aaug;
-    STAG_CUDA_TRY(cudaMalloc(&tc->err, sizeof(int)));
+    STAG_CUDA_TRY(dev_malloc(&tc->err, sizeof(int)));
     STAG_CUDA_TRY(cudaMemset(tc->err, 0, sizeof(int)));
     STAG_CUDA_TRY(cudaMallocHost(&tc->err_host, sizeof(int)));
     return 0;
@@ -1305,20 +1345,23 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     tc->T = ceil_div(h->n, tc->BN);
     tc->n_pad = tc->T * tc->BN;
     const int Kp = tc->Kp;
-    STAG_CUDA_TRY(cudaMalloc(&tc->b_hi, tc->n_pad * Kp * sizeof(__half)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->b_lo, tc->n_pad * Kp * sizeof(__half)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->b_aug, tc->n_pad * 16 * sizeof(__half)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->a_aug, BM * 16 * sizeof(__half)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->tinfo, tc->T * 4 * sizeof(float)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->cent, tc->T * Kp * sizeof(float)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->cg, Kp * sizeof(float)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->xs, h->n * h->d * sizeof(float)));
-    STAG_CUDA_TRY(cudaMemcpyAsync(tc->xs, dX, h->n * h->d * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    STAG_CUDA_TRY(cudaMalloc(&tc->tsum, tc->T * Kp * sizeof(double)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->vmax_bits, sizeof(unsigned)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->xmax_bits, sizeof(unsigned)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->scales, 4 * sizeof(float)));
-    STAG_CUDA_TRY(cudaMalloc(&tc->err, sizeof(int)));
+    STAG_CUDA_TRY(dev_malloc(&tc->b_hi, tc->n_pad * Kp * sizeof(__half)));
+    STAG_CUDA_TRY(dev_malloc(&tc->b_lo, tc->n_pad * Kp * sizeof(__half)));
+    STAG_CUDA_TRY(dev_malloc(&tc->b_aug, tc->n_pad * 16 * sizeof(__half)));
+    STAG_CUDA_TRY(dev_malloc(&tc->a_aug, BM * 16 * sizeof(__half)));
+    STAG_CUDA_TRY(dev_malloc(&tc->tinfo, tc->T * 4 * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&tc->cent, tc->T * Kp * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&tc->cg, Kp * sizeof(float)));
+    if (h->tc_check && h->d <= kPrunedMaxD) {
+        // only the pruned recompute of flagged queries reads the ordered FP32 points
+        STAG_CUDA_TRY(dev_malloc(&tc->xs, h->n * h->d * sizeof(float)));
+        STAG_CUDA_TRY(cudaMemcpyAsync(tc->xs, dX, h->n * h->d * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    }
+    STAG_CUDA_TRY(dev_malloc(&tc->tsum, tc->T * Kp * sizeof(double)));
+    STAG_CUDA_TRY(dev_malloc(&tc->vmax_bits, sizeof(unsigned)));
+    STAG_CUDA_TRY(dev_malloc(&tc->xmax_bits, sizeof(unsigned)));
+    STAG_CUDA_TRY(dev_malloc(&tc->scales, 4 * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&tc->err, sizeof(int)));
     STAG_CUDA_TRY(cudaMallocHost(&tc->err_host, sizeof(int)));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->err, 0, sizeof(int), s));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->vmax_bits, 0, sizeof(unsigned), s));
@@ -1353,8 +1396,8 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         cudaFree(tc->a_lo);
         tc->a_hi = tc->a_lo = nullptr;
         tc->a_rows_cap = 0;
-        STAG_CUDA_TRY(cudaMalloc(&tc->a_hi, m_pad * Kp * sizeof(__half)));
-        STAG_CUDA_TRY(cudaMalloc(&tc->a_lo, m_pad * Kp * sizeof(__half)));
+        STAG_CUDA_TRY(dev_malloc(&tc->a_hi, m_pad * Kp * sizeof(__half)));
+        STAG_CUDA_TRY(dev_malloc(&tc->a_lo, m_pad * Kp * sizeof(__half)));
         tc->a_rows_cap = m_pad;
         int rc = make_map(&tc->map_ahi, tc->a_hi, m_pad, Kp, BM);
         if (!rc) rc = make_map(&tc->map_alo, tc->a_lo, m_pad, Kp, BM);
@@ -1370,19 +1413,19 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         tc->ub = nullptr;
         tc->fix_idx = nullptr;
         tc->unorm_cap = 0;
-        STAG_CUDA_TRY(cudaMalloc(&tc->unorm, m_pad * sizeof(float)));
-        STAG_CUDA_TRY(cudaMalloc(&tc->qbad, m_pad * sizeof(int)));
-        STAG_CUDA_TRY(cudaMalloc(&tc->ub, m_pad * sizeof(unsigned)));
-        STAG_CUDA_TRY(cudaMalloc(&tc->fix_idx, m_pad * sizeof(int)));
+        STAG_CUDA_TRY(dev_malloc(&tc->unorm, m_pad * sizeof(float)));
+        STAG_CUDA_TRY(dev_malloc(&tc->qbad, m_pad * sizeof(int)));
+        STAG_CUDA_TRY(dev_malloc(&tc->ub, m_pad * sizeof(unsigned)));
+        STAG_CUDA_TRY(dev_malloc(&tc->fix_idx, m_pad * sizeof(int)));
         tc->unorm_cap = m_pad;
     }
-    if (!tc->fix_count) STAG_CUDA_TRY(cudaMalloc(&tc->fix_count, sizeof(int)));
+    if (!tc->fix_count) STAG_CUDA_TRY(dev_malloc(&tc->fix_count, sizeof(int)));
     const int64_t need = tc->T * m_pad;
     if (tc->rt_cap < need) {
         cudaFree(tc->rowterm);
         tc->rowterm = nullptr;
         tc->rt_cap = 0;
-        STAG_CUDA_TRY(cudaMalloc(&tc->rowterm, need * sizeof(float)));
+        STAG_CUDA_TRY(dev_malloc(&tc->rowterm, need * sizeof(float)));
         tc->rt_cap = need;
     }
     return 0;
@@ -1414,17 +1457,16 @@ int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit) {
     if (rc) return rc;
     int64_t qt, sp, tps;
     plan_units(h, m, tiles_per_unit, &qt, &sp, &tps);
-    // the plain form's recompute path shares the partials buffer and needs its tiled copy
-    rc = simt_reserve(h, m);
-    if (rc) return rc;
-    rc = ensure_partials(h, sp * m);
+    // above d = 16 flagged queries are recomputed by the plain form (tiled copy, partials)
+    if (h->d > kPrunedMaxD) rc = simt_reserve(h, m);
+    if (!rc) rc = ensure_partials(h, sp * m);
     if (rc) return rc;
     if (tc->part_w_cap < sp * m) {
         ++h->scratch_epoch;
         cudaFree(tc->part_w);
         tc->part_w = nullptr;
         tc->part_w_cap = 0;
-        STAG_CUDA_TRY(cudaMalloc(&tc->part_w, sp * m * sizeof(double)));
+        STAG_CUDA_TRY(dev_malloc(&tc->part_w, sp * m * sizeof(double)));
         tc->part_w_cap = sp * m;
     }
     return 0;
@@ -1486,8 +1528,7 @@ static void fill_inst(const stag_kde *h, int64_t m, int64_t q_tiles, int64_t spl
 }
 
 // FP64 combine with the per-query error estimate, then the FP32 recompute of the flagged
-// queries: over the tiles that can matter (tc_fixup_pruned_kernel) for d <= 16, by the
-// plain form over all points above.
+// queries over the tiles that can matter (tc_fixup_pruned_kernel).
 static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
     TcData *tc = h->tc;
     const bool check = h->tc_check;
@@ -1498,8 +1539,9 @@ static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, do
         tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
     STAG_CUDA_TRY(cudaGetLastError());
     if (!check) return 0;
+    // Above d = 16 the per-query pass would re-read its kept tiles once per flagged query;
+    // the plain form's tiled kernel over all points shares each load across 64 queries.
     if (h->d > kPrunedMaxD) return simt_fixup_rows(h, dQ, m, tc->fix_idx, tc->fix_count, dOut, s);
-    // low d: distances spread widely, so most tiles drop out of a flagged query's sum
     const unsigned grid = (unsigned)(h->sm_count * 8);
     const size_t smem = (size_t)(((h->d + 3) & ~3) * sizeof(float) + kPrunedWarps * (sizeof(double) + 2 * sizeof(float)));
     const float c = (float)(h->a * 1.4426950408889634);
@@ -1533,10 +1575,10 @@ int64_t tc_fill_inst(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t u
 }
 
 int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total_units, int *err, int sm_count,
-                    cudaStream_t s) {
+                    uint64_t wait_ns, cudaStream_t s) {
     static TcInst unused{};  // kernel parameter slot; the kernel reads the table
     return launch_tc_any(Kp, eg, unused, reinterpret_cast<const TcInst *>(table), n_inst, total_units, err, sm_count,
-                         s);
+                         wait_ns, s);
 }
 
 int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
@@ -1559,7 +1601,7 @@ int tc_query(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t
     fill_inst(h, m, q_tiles, splits, tps, 0, &inst);
     prof_start(h, s);
     rc = launch_tc_any(tc->Kp, h->tune_eg ? h->tune_eg : tc_epilogue_groups(), inst, nullptr, 1, inst.units,
-                       tc->err, h->sm_count, s);
+                       tc->err, h->sm_count, h->wait_ns, s);
     prof_stop(h, s, (double)m * (double)h->n);
     if (rc) return rc;
     return tc_finish(h, dQ, m, splits, dOut, s);

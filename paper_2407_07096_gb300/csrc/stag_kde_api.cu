@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
+#include <stdlib.h>
 #include <cstdio>
 #include <new>
 #include <string>
@@ -37,8 +39,30 @@ int fail(int code, const std::string &msg) {
 
 int cuda_fail(cudaError_t e, const char *what) {
     g_last_error = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
-    g_last_code = STAG_KDE_ECUDA;
-    return STAG_KDE_ECUDA;
+    // an allocation the device could not satisfy is reported as out of memory
+    g_last_code = e == cudaErrorMemoryAllocation ? STAG_KDE_ENOMEM : STAG_KDE_ECUDA;
+    return g_last_code;
+}
+
+cudaError_t dev_malloc_bytes(void **p, size_t bytes) {
+    static std::mutex mu;
+    static std::string armed;  // the variable's value the count started from
+    static long long count = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        const char *v = getenv("STAG_KDE_INJECT_ALLOC_FAIL");
+        const std::string now = v ? v : "";
+        if (now != armed) {
+            armed = now;
+            count = 0;
+        }
+        const long long k = now.empty() ? 0 : atoll(now.c_str());
+        if (k > 0 && ++count == k) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
 }
 
 static cudaEvent_t prof_event(stag_kde *h) {
@@ -150,6 +174,7 @@ stag_kde *make_view(stag_kde *base) {
     v->tc_check = base->tc_check;
     v->tune_eg = base->tune_eg;
     v->tune_tiles_per_unit = base->tune_tiles_per_unit;
+    v->wait_ns = base->wait_ns;
     v->is_view = true;
     v->xt = base->xt;
     v->n_tiles = base->n_tiles;
@@ -158,7 +183,7 @@ stag_kde *make_view(stag_kde *base) {
     v->sm_count = base->sm_count;
     cudaError_t e;
     if ((e = cudaStreamCreateWithFlags(&v->stream, cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaMalloc(&v->flag_dev, sizeof(int))) != cudaSuccess ||
+        (e = dev_malloc(&v->flag_dev, sizeof(int))) != cudaSuccess ||
         (e = cudaMallocHost(&v->flag_host, sizeof(int))) != cudaSuccess) {
         cuda_fail(e, "view set-up");
         free_handle(v);
@@ -209,7 +234,7 @@ int ensure_bytes(void **p, int64_t *cap, int64_t bytes) {
     cudaFree(*p);
     *p = nullptr;
     *cap = 0;
-    STAG_CUDA_TRY(cudaMalloc(p, bytes));
+    STAG_CUDA_TRY(dev_malloc(p, bytes));
     *cap = bytes;
     return 0;
 }
@@ -292,17 +317,17 @@ stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, d
         return bail("cudaDeviceGetAttribute", e);
     if ((e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail("cudaStreamCreate", e);
-    if ((e = cudaMalloc(&h->flag_dev, sizeof(int))) != cudaSuccess) return bail("cudaMalloc(flag)", e);
+    if ((e = dev_malloc(&h->flag_dev, sizeof(int))) != cudaSuccess) return bail("dev_malloc(flag)", e);
     if ((e = cudaMallocHost(&h->flag_host, sizeof(int))) != cudaSuccess) return bail("cudaMallocHost", e);
 
     const size_t bytes = (size_t)(n * d) * elem_size(dtype);
     if (dtype == STAG_KDE_F64) {
-        if ((e = cudaMalloc(&h->x64, bytes)) != cudaSuccess) return bail("cudaMalloc(X)", e);
+        if ((e = dev_malloc(&h->x64, bytes)) != cudaSuccess) return bail("dev_malloc(X)", e);
         if ((e = cudaMemcpyAsync(h->x64, X, bytes, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
             return bail("cudaMemcpy(X)", e);
     } else {
         float *dX = nullptr;
-        if ((e = cudaMalloc(&dX, bytes)) != cudaSuccess) return bail("cudaMalloc(X)", e);
+        if ((e = dev_malloc(&dX, bytes)) != cudaSuccess) return bail("dev_malloc(X)", e);
         int rc = 0;
         if ((e = cudaMemcpyAsync(dX, X, bytes, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess) {
             cudaFree(dX);
@@ -314,8 +339,8 @@ stag_kde_t *stag_kde_create_ex(const void *X, int dtype, int64_t n, int64_t d, d
         if (!rc && form == STAG_KDE_FORM_TC) {
             // tensor-core form: tiles of spatially coherent points (k-d order)
             float *dXs = nullptr;
-            if ((e = cudaMalloc(&dXs, bytes)) != cudaSuccess) {
-                rc = cuda_fail(e, "cudaMalloc(ordered X)");
+            if ((e = dev_malloc(&dXs, bytes)) != cudaSuccess) {
+                rc = cuda_fail(e, "dev_malloc(ordered X)");
             } else {
                 rc = kd_reorder(dX, n, d, tc_tile_points(d), dXs, h->stream);
                 if (!rc) rc = tc_prepare_points(h, dXs);
@@ -442,28 +467,37 @@ int stag_kde_query_subset(stag_kde_t *h, const float *Q, int64_t m, const int64_
         if (!h->copy_stream[i]) STAG_CUDA_TRY(cudaStreamCreateWithFlags(&h->copy_stream[i], cudaStreamNonBlocking));
         if (!h->copy_done[i]) STAG_CUDA_TRY(cudaEventCreateWithFlags(&h->copy_done[i], cudaEventDisableTiming));
     }
-    const int64_t half = nnz / 2;
-    if (half > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dIdx, idx, half * 8, cudaMemcpyHostToDevice, h->copy_stream[0]));
-    if (nnz > half)
-        STAG_CUDA_TRY(cudaMemcpyAsync(dIdx + half, idx + half, (nnz - half) * 8, cudaMemcpyHostToDevice,
-                                      h->copy_stream[1]));
-    for (int i = 0; i < 2; ++i) STAG_CUDA_TRY(cudaEventRecord(h->copy_done[i], h->copy_stream[i]));
-    STAG_CUDA_TRY(cudaMemcpyAsync(dOff, off, (m + 1) * 8, cudaMemcpyHostToDevice, s));
-    if (W && nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dW, W, nnz * 4, cudaMemcpyHostToDevice, s));
-    STAG_CUDA_TRY(cudaMemcpyAsync(dQ, Q, m * h->d * 4, cudaMemcpyHostToDevice, s));
-    STAG_CUDA_TRY(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
-    rc = launch_check_finite_f32(dQ, m * h->d, h->flag_dev, s, 4);
-    for (int i = 0; i < 2 && !rc; ++i) STAG_CUDA_TRY(cudaStreamWaitEvent(s, h->copy_done[i], 0));
-    if (!rc) rc = subset_check_entries(dIdx, W ? dW : nullptr, nnz, h->n, h->flag_dev, s);
-    if (!rc) rc = subset_query(h, dQ, m, dOff, dIdx, W ? dW : nullptr, h->out_dev, s, (double)nnz);
+    // Everything from the first copy on reports through rc: on any failure the copy streams
+    // and the handle's stream are drained before the return, so that no queued copy reads
+    // the caller's buffers afterwards.
+    auto enqueue = [&]() -> int {
+        const int64_t half = nnz / 2;
+        if (half > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dIdx, idx, half * 8, cudaMemcpyHostToDevice, h->copy_stream[0]));
+        if (nnz > half)
+            STAG_CUDA_TRY(cudaMemcpyAsync(dIdx + half, idx + half, (nnz - half) * 8, cudaMemcpyHostToDevice,
+                                          h->copy_stream[1]));
+        for (int i = 0; i < 2; ++i) STAG_CUDA_TRY(cudaEventRecord(h->copy_done[i], h->copy_stream[i]));
+        STAG_CUDA_TRY(cudaMemcpyAsync(dOff, off, (m + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (W && nnz > 0) STAG_CUDA_TRY(cudaMemcpyAsync(dW, W, nnz * 4, cudaMemcpyHostToDevice, s));
+        STAG_CUDA_TRY(cudaMemcpyAsync(dQ, Q, m * h->d * 4, cudaMemcpyHostToDevice, s));
+        STAG_CUDA_TRY(cudaMemsetAsync(h->flag_dev, 0, sizeof(int), s));
+        int r = launch_check_finite_f32(dQ, m * h->d, h->flag_dev, s, 4);
+        if (r) return r;
+        for (int i = 0; i < 2; ++i) STAG_CUDA_TRY(cudaStreamWaitEvent(s, h->copy_done[i], 0));
+        r = subset_check_entries(dIdx, W ? dW : nullptr, nnz, h->n, h->flag_dev, s);
+        if (r) return r;
+        r = subset_query(h, dQ, m, dOff, dIdx, W ? dW : nullptr, h->out_dev, s, (double)nnz);
+        if (r) return r;
+        STAG_CUDA_TRY(cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return 0;
+    };
+    rc = enqueue();
     if (rc) {
-        // the caller's buffers must not be read after the return
         cudaStreamSynchronize(h->copy_stream[0]);
         cudaStreamSynchronize(h->copy_stream[1]);
         cudaStreamSynchronize(s);
         return rc;
     }
-    STAG_CUDA_TRY(cudaMemcpyAsync(h->flag_host, h->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     STAG_CUDA_TRY(cudaStreamSynchronize(s));
     if (*h->flag_host & 4) return fail(STAG_KDE_EINVAL, "Q has a non-finite value or |q| > 1e15");
     if (*h->flag_host & 1) return fail(STAG_KDE_EINVAL, "an index is outside [0, n)");
@@ -501,6 +535,13 @@ int stag_kde_info(const stag_kde_t *h, int64_t *n, int64_t *d, double *a, int *d
 }
 
 void stag_kde_destroy(stag_kde_t *h) { free_handle(h); }
+
+int stag_kde_set_wait_limit(stag_kde_t *h, int64_t limit_ns) {
+    if (!h) return fail(STAG_KDE_EINVAL, "handle is NULL");
+    if (limit_ns < 0 || limit_ns > 60000000000ll) return fail(STAG_KDE_EINVAL, "wait limit must be in [0, 60 s]");
+    h->wait_ns = limit_ns == 0 ? 2000000000ull : (uint64_t)limit_ns;
+    return 0;
+}
 
 int stag_kde_last_recomputed(stag_kde_t *h, int64_t *count) {
     if (!h || !count) return fail(STAG_KDE_EINVAL, "handle or count is NULL");

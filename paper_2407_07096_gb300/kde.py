@@ -97,6 +97,10 @@ class ExactGaussianKDE:
                                              ctypes.c_void_p(s.cuda_stream)))
         return out
 
+    def set_wait_limit(self, limit_ns: int):
+        """Limit of each bounded wait in the tensor-core kernel (0: the default, 2 s)."""
+        L.check(self._lib.stag_kde_set_wait_limit(self._h, int(limit_ns)))
+
     def last_recomputed(self) -> int:
         """Queries of the last call that the tensor-core error estimate sent to FP32."""
         c = ctypes.c_int64()
