@@ -134,11 +134,17 @@ int simt_points_rows(stag_kde *h, float *out, cudaStream_t s);
 int launch_subtract(double *v, int64_t count, double one, cudaStream_t s);
 // Sizes the plain form's scratch (tiled queries, partials) for queries of up to m rows.
 int simt_reserve(stag_kde *h, int64_t m);
-// Recomputes with the plain FP32 form the rows idx[0 .. *count) of dQ (device count)
-// and writes their densities to dOut[idx[j]].
-int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
-                    cudaStream_t s);
 int ensure_qt(stag_kde *h, int64_t floats);
+// Grouped pruned recompute (tensor-core form, d > 16): the plain form's register-tiled
+// kernel over lists of kept point tiles per query group (see kde_simt.cu), the gather of
+// rows idx[0 .. *count) into tile-transposed query tiles, and a tile-transposed copy of
+// row-major points (the k-d ordered set).
+int simt_list_launch(const stag_kde *h, const float *xt, const float *qt, const int *kept, int64_t kstride,
+                     const int *kcount, const int *item_off, const int *n_groups, int seg, int per, double *part_sum,
+                     float *part_shift, cudaStream_t s);
+int simt_gather_rows(const stag_kde *h, const float *dQ, const int *idx, const int *count, int64_t m_cap, float *qt,
+                     cudaStream_t s);
+int simt_tiles_from_rows(const stag_kde *h, const float *rows, float *out, cudaStream_t s);
 int launch_check_finite_f32(const float *p, int64_t count, int *dflag, cudaStream_t s, int bit = 1);
 int launch_check_finite_f64(const double *p, int64_t count, int *dflag, cudaStream_t s);
 

@@ -49,6 +49,12 @@ struct BatchPlan {
     int *d_err = nullptr;
     int *h_err = nullptr;  // pinned copy written at the end of every replay
     cudaStream_t cap = nullptr;
+    // side streams: the instances' preparation and finish chains are spread over them so
+    // that the small kernels of different instances overlap on the device (in the graph
+    // they become parallel branches between a fork and a join event)
+    static constexpr int kSide = 8;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, joined[kSide] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t launches_per_run = 0;
@@ -74,6 +80,11 @@ void free_plan(BatchPlan *p) {
     cudaFree(p->d_err);
     if (p->h_err) cudaFreeHost(p->h_err);
     if (p->cap) cudaStreamDestroy(p->cap);
+    for (int i = 0; i < BatchPlan::kSide; ++i) {
+        if (p->side[i]) cudaStreamDestroy(p->side[i]);
+        if (p->joined[i]) cudaEventDestroy(p->joined[i]);
+    }
+    if (p->fork) cudaEventDestroy(p->fork);
     if (prev >= 0) cudaSetDevice(prev);
     delete p;
 }
@@ -125,29 +136,51 @@ int build_tables(BatchPlan *p) {
     return 0;
 }
 
-// Queues the whole batch on stream s.
+// Queues the whole batch on stream s: the instances' query preparation spread over the
+// side streams, one persistent tensor-core launch per operand width on s, then the
+// instances' combine and recompute chains spread over the side streams again; s waits
+// for every side stream at the end (fork/join with events, so the order holds both when
+// run directly and when captured into the graph).
 int enqueue(BatchPlan *p, cudaStream_t s) {
     int rc = 0;
+    auto fork = [&]() -> int {
+        STAG_CUDA_TRY(cudaEventRecord(p->fork, s));
+        for (int k = 0; k < BatchPlan::kSide; ++k) STAG_CUDA_TRY(cudaStreamWaitEvent(p->side[k], p->fork, 0));
+        return 0;
+    };
+    auto join = [&]() -> int {
+        for (int k = 0; k < BatchPlan::kSide; ++k) {
+            STAG_CUDA_TRY(cudaEventRecord(p->joined[k], p->side[k]));
+            STAG_CUDA_TRY(cudaStreamWaitEvent(s, p->joined[k], 0));
+        }
+        return 0;
+    };
+    auto side_of = [&](size_t i) { return p->side[i % BatchPlan::kSide]; };
+    rc = fork();
     for (size_t i = 0; i < p->hs.size() && !rc; ++i) {
         stag_kde *h = p->hs[i];
         if (p->ms[i] == 0) continue;
-        if (is_tc(h)) rc = tc_prep_public(h, (const float *)p->qs[i], p->ms[i], s);
+        if (is_tc(h)) rc = tc_prep_public(h, (const float *)p->qs[i], p->ms[i], side_of(i));
     }
+    if (!rc) rc = join();
     for (auto &c : p->classes) {
         if (rc) break;
         rc = tc_launch_table(c.Kp, p->eg, c.d_table, c.n_inst, c.total_units, p->d_err, p->hs[0]->sm_count,
                              p->wait_ns, s);
     }
+    if (!rc) rc = fork();
     for (size_t i = 0; i < p->hs.size() && !rc; ++i) {
         stag_kde *h = p->hs[i];
         if (p->ms[i] == 0) continue;
+        cudaStream_t si = side_of(i);
         if (is_tc(h))
-            rc = tc_finish_public(h, (const float *)p->qs[i], p->ms[i], p->splits[i], p->outs[i], s);
+            rc = tc_finish_public(h, (const float *)p->qs[i], p->ms[i], p->splits[i], p->outs[i], si);
         else if (h->form == STAG_KDE_FORM_SIMT_F32)
-            rc = simt_query_f32(h, (const float *)p->qs[i], p->ms[i], p->outs[i], s, nullptr);
+            rc = simt_query_f32(h, (const float *)p->qs[i], p->ms[i], p->outs[i], si, nullptr);
         else
-            rc = simt_query_f64(h, (const double *)p->qs[i], p->ms[i], p->outs[i], s, nullptr);
+            rc = simt_query_f64(h, (const double *)p->qs[i], p->ms[i], p->outs[i], si, nullptr);
     }
+    if (!rc) rc = join();
     return rc;
 }
 
@@ -201,6 +234,11 @@ int build_plan(BatchPlan *p) {
     // let every earlier piece of work on the device finish first
     STAG_CUDA_TRY(cudaDeviceSynchronize());
     STAG_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    for (int k = 0; k < BatchPlan::kSide; ++k) {
+        STAG_CUDA_TRY(cudaStreamCreateWithFlags(&p->side[k], cudaStreamNonBlocking));
+        STAG_CUDA_TRY(cudaEventCreateWithFlags(&p->joined[k], cudaEventDisableTiming));
+    }
+    STAG_CUDA_TRY(cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming));
     STAG_CUDA_TRY(dev_malloc(&p->d_err, sizeof(int)));
     STAG_CUDA_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
     STAG_CUDA_TRY(cudaMallocHost(&p->h_err, sizeof(int)));

@@ -105,22 +105,19 @@ __device__ __forceinline__ void merge(RowAcc &r, double oacc, float oshift) {
     r.shift = sm;
 }
 
-// One work item: query tile `qtile` (64 rows) against the point tiles of range `split`.
-// Rows at or past m_real are computed on zero padding and not stored; partials use the
-// row stride m.
-template <bool kSingleChunk, int KERN>
+// One work item: a query tile of 64 rows (qbase, tile-transposed) against `ntiles` point
+// tiles, tile_at(i) giving the index of the i-th. Rows at or past rows_valid are
+// computed on zero padding and not stored; the partials of row r go to out_sum[r] and
+// out_shift[r].
+template <bool kSingleChunk, int KERN, class TileAt>
 __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], float (*sQ)[kSimtKC * kSimtTile],
-                                          const float *__restrict__ xt, int64_t n, int64_t n_tiles,
-                                          const float *__restrict__ qt, int64_t m, int64_t m_real, int d_pad,
-                                          float negc, int64_t tiles_per_split, double *__restrict__ part_sum,
-                                          float *__restrict__ part_shift, int64_t qtile, int64_t split) {
+                                          const float *__restrict__ xt, int64_t n, const float *__restrict__ qbase,
+                                          int d_pad, float negc, int64_t ntiles, TileAt tile_at, int64_t rows_valid,
+                                          double *__restrict__ out_sum, float *__restrict__ out_shift) {
     const int tid = threadIdx.x;
     const int tx = tid & 15;  // point group: points 4*tx .. 4*tx+3 of the tile
     const int ty = tid >> 4;  // query group: rows 4*ty .. 4*ty+3 of the block
-    const int64_t t0 = (int64_t)split * tiles_per_split;
-    const int64_t t1 = min(n_tiles, t0 + tiles_per_split);
     const int nch = (d_pad + kSimtKC - 1) / kSimtKC;
-    const float *qbase = qt + qtile * (int64_t)d_pad * kSimtTile;
 
     RowAcc row[4];
 #pragma unroll
@@ -142,8 +139,8 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
         const int nvec = d_pad * (kSimtTile / 4);
         for (int v = tid; v < nvec; v += 256) cp_async16(&sQ[0][v * 4], qbase + v * 4);
     }
-    const int64_t iters = (t1 - t0) * nch;
-    if (iters > 0) load(0, t0, 0);
+    const int64_t iters = ntiles * nch;
+    if (iters > 0) load(0, tile_at(0), 0);
     cp_async_commit();
 
     // squared distances of the 4 x 4 pairs, as packed column pairs (4*tx+0,1) and (+2,3)
@@ -155,7 +152,7 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
     for (int64_t it = 0; it < iters; ++it) {
         const int stage = (int)(it & 1);
         if (it + 1 < iters) {
-            load(stage ^ 1, t0 + (it + 1) / nch, (int)((it + 1) % nch));
+            load(stage ^ 1, tile_at((it + 1) / nch), (int)((it + 1) % nch));
             cp_async_commit();
             cp_async_wait<1>();
         } else {
@@ -198,7 +195,7 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
         __syncthreads();
 
         if (ch == nch - 1) {
-            const int64_t t = t0 + it / nch;
+            const int64_t t = tile_at(it / nch);
             const int64_t col0 = t * kSimtTile + tx * 4;
             const int valid = (int)max((int64_t)0, min((int64_t)4, n - col0));
 #pragma unroll
@@ -238,36 +235,82 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
     if (tx == 0) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int64_t q = qtile * kSimtTile + ty * 4 + i;
-            if (q < m_real) {
-                part_sum[(int64_t)split * m + q] = row[i].acc64;
-                part_shift[(int64_t)split * m + q] = row[i].shift;
+            const int r = ty * 4 + i;
+            if (r < rows_valid) {
+                out_sum[r] = row[i].acc64;
+                out_shift[r] = row[i].shift;
             }
         }
     }
 }
 
+// The contiguous point tiles of split `split` against query tile `qtile`; partials of
+// query q at part_sum[split * m + q] (rows from m_real on are not stored).
+template <bool kSingleChunk, int KERN>
+__device__ __forceinline__ void simt_split_item(float (*sX)[kSimtKC * kSimtTile], float (*sQ)[kSimtKC * kSimtTile],
+                                                const float *__restrict__ xt, int64_t n, int64_t n_tiles,
+                                                const float *__restrict__ qt, int64_t m, int64_t m_real, int d_pad,
+                                                float negc, int64_t tiles_per_split, double *__restrict__ part_sum,
+                                                float *__restrict__ part_shift, int64_t qtile, int64_t split) {
+    const int64_t t0 = split * tiles_per_split;
+    const int64_t t1 = min(n_tiles, t0 + tiles_per_split);
+    const int64_t off = split * m + qtile * kSimtTile;
+    simt_item<kSingleChunk, KERN>(sX, sQ, xt, n, qt + qtile * (int64_t)d_pad * kSimtTile, d_pad, negc,
+                                  max((int64_t)0, t1 - t0), [t0](int64_t i) { return t0 + i; },
+                                  m_real - qtile * kSimtTile, part_sum + off, part_shift + off);
+}
+
 template <bool kSingleChunk, int KERN>
 __global__ void __launch_bounds__(256, 2)
 kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, const float *__restrict__ qt, int64_t m,
-                    int d_pad, float negc, int64_t tiles_per_split, int64_t splits, double *__restrict__ part_sum,
-                    float *__restrict__ part_shift, const int *__restrict__ count) {
+                    int d_pad, float negc, int64_t tiles_per_split, double *__restrict__ part_sum,
+                    float *__restrict__ part_shift) {
     __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
     __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
-    if (!count) {
-        // one block per (query tile, split)
-        simt_item<kSingleChunk, KERN>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum,
-                                      part_shift, blockIdx.x, blockIdx.y);
-        return;
-    }
-    // `count` (device memory): only the first *count query rows are real; a fixed grid
-    // walks the (query tile, split) items those rows need
-    const int64_t rows = *count;
-    const int64_t items = ((rows + kSimtTile - 1) / kSimtTile) * splits;
-    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    // one block per (query tile, split)
+    simt_split_item<kSingleChunk, KERN>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum,
+                                        part_shift, blockIdx.x, blockIdx.y);
+}
+
+// The grouped recompute of the tensor-core form's flagged queries (kde_tc.cu): work item
+// w belongs to query group g (item_off[g] <= w < item_off[g + 1]; groups = *n_groups) and
+// covers the group's kept point tiles [s * seg, min(kcount[g], (s + 1) * seg)) of the
+// list kept[g * kstride ..], s = w - item_off[g]; each kept tile is `per` consecutive
+// 64-point tiles of xt. Query group g is tile g of qt (64 gathered rows). The partials of
+// row r go to part_sum[w * 64 + r]. A fixed grid walks the items (counts on the device).
+template <bool kSingleChunk, int KERN>
+__global__ void __launch_bounds__(256, 2)
+kde_simt_f32_list_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, const float *__restrict__ qt,
+                         int d_pad, float negc, const int *__restrict__ kept, int64_t kstride,
+                         const int *__restrict__ kcount, const int *__restrict__ item_off,
+                         const int *__restrict__ n_groups, int seg, int per, double *__restrict__ part_sum,
+                         float *__restrict__ part_shift) {
+    __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
+    __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
+    const int G = *n_groups;
+    const int total = G > 0 ? item_off[G] : 0;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
         __syncthreads();  // the previous item's shared-memory reads are done
-        simt_item<kSingleChunk, KERN>(sX, sQ, xt, n, n_tiles, qt, m, rows, d_pad, negc, tiles_per_split, part_sum,
-                                      part_shift, w / splits, w % splits);
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_off[mid] <= w)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int g = lo;
+        const int k0 = (w - item_off[g]) * seg;
+        const int k1 = min(kcount[g], k0 + seg);
+        const int *list = kept + (int64_t)g * kstride + k0;
+        // the point set's last tile may cover fewer than `per` 64-point tiles; it can only
+        // be the list's last entry (the lists ascend), whose tail is enumerated last
+        int64_t nt = (int64_t)(k1 - k0) * per;
+        if (k1 > k0) nt -= max((int64_t)0, ((int64_t)list[k1 - k0 - 1] + 1) * per - n_tiles);
+        simt_item<kSingleChunk, KERN>(
+            sX, sQ, xt, n, qt + (int64_t)g * d_pad * kSimtTile, d_pad, negc, nt,
+            [list, per](int64_t i) { return (int64_t)list[i / per] * per + i % per; }, kSimtTile,
+            part_sum + (int64_t)w * kSimtTile, part_shift + (int64_t)w * kSimtTile);
     }
 }
 
@@ -351,21 +394,6 @@ __global__ void gather_rows_tiles_kernel(const float *__restrict__ Q, int64_t d,
     }
 }
 
-// out[idx[j]] = sum over splits of part_sum * 2^part_shift (FP64, split order), j < *count.
-__global__ void combine_scatter_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
-                                       int64_t m_stride, int splits, const int *__restrict__ idx,
-                                       const int *__restrict__ count, double scale, double *__restrict__ out) {
-    const int64_t cnt = *count;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
-        float smax = -INFINITY;
-        for (int k = 0; k < splits; ++k) smax = fmaxf(smax, part_shift[(int64_t)k * m_stride + j]);
-        double tot = 0.0;
-        for (int k = 0; k < splits; ++k)
-            tot += ldexp(part_sum[(int64_t)k * m_stride + j], clamp_exp(part_shift[(int64_t)k * m_stride + j] - smax));
-        out[idx[j]] = ldexp(tot, clamp_exp(smax)) * scale;
-    }
-}
-
 int grid_for(int64_t total, int threads) {
     return (int)std::min<int64_t>(ceil_div(total, threads), 152 * 16);
 }
@@ -425,25 +453,23 @@ int simt_prepare_points(stag_kde *h, const float *dX) {
 
 // Launches the FP32 kernel instance for the handle's operand width and kernel function.
 template <int KERN>
-void launch_simt_kern(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, float negc, int64_t tps,
-                      int64_t splits, const int *count) {
+void launch_simt_kern(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, float negc, int64_t tps) {
     if (h->d_pad <= kSimtKC)
         kde_simt_f32_kernel<true, KERN><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
-                                                             splits, h->part.sum, h->part.shift, count);
+                                                             h->part.sum, h->part.shift);
     else
         kde_simt_f32_kernel<false, KERN><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
-                                                              splits, h->part.sum, h->part.shift, count);
+                                                              h->part.sum, h->part.shift);
 }
-void launch_simt(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, int64_t tps, int64_t splits,
-                 const int *count) {
+void launch_simt(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, int64_t tps) {
     const float negc = (float)(-h->a * 1.4426950408889634);  // -a log2(e)
     switch (h->kernel) {
         case STAG_KDE_KERNEL_EXPONENTIAL:
-            return launch_simt_kern<STAG_KDE_KERNEL_EXPONENTIAL>(h, grid, s, m, negc, tps, splits, count);
+            return launch_simt_kern<STAG_KDE_KERNEL_EXPONENTIAL>(h, grid, s, m, negc, tps);
         case STAG_KDE_KERNEL_LOGISTIC:
-            return launch_simt_kern<STAG_KDE_KERNEL_LOGISTIC>(h, grid, s, m, negc, tps, splits, count);
+            return launch_simt_kern<STAG_KDE_KERNEL_LOGISTIC>(h, grid, s, m, negc, tps);
         default:
-            return launch_simt_kern<STAG_KDE_KERNEL_GAUSSIAN>(h, grid, s, m, negc, tps, splits, count);
+            return launch_simt_kern<STAG_KDE_KERNEL_GAUSSIAN>(h, grid, s, m, negc, tps);
     }
 }
 
@@ -478,45 +504,19 @@ int simt_query_f32(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaSt
     dim3 grid((unsigned)q_tiles, (unsigned)splits);
     count_launch();
     prof_start(h, s);
-    launch_simt(h, grid, s, m, tps, splits, nullptr);
+    launch_simt(h, grid, s, m, tps);
     prof_stop(h, s, (double)m * (double)h->n);
     STAG_CUDA_TRY(cudaGetLastError());
     return launch_combine(h->part.sum, h->part.shift, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
                           dOut, s);
 }
 
-// The recompute path serves few rows (only those the tensor-core estimate flags), so it
-// splits the point set finely and walks the work with a fixed grid.
-static int64_t fixup_splits(const stag_kde *h) { return std::max<int64_t>(1, std::min<int64_t>(h->n_tiles, 64)); }
-
 int simt_reserve(stag_kde *h, int64_t m) {
     const int64_t q_tiles = ceil_div(m, kSimtTile);
     int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
     if (rc) return rc;
     const int64_t tps = choose_tiles_per_split(h, q_tiles);
-    const int64_t splits = std::max(ceil_div(h->n_tiles, tps), ceil_div(h->n_tiles, ceil_div(h->n_tiles, fixup_splits(h))));
-    return ensure_partials(h, splits * m);
-}
-
-int simt_fixup_rows(stag_kde *h, const float *dQ, int64_t m, const int *idx, const int *count, double *dOut,
-                    cudaStream_t s) {
-    // the row set is only known on the device: size everything for all m rows and let
-    // the kernels walk only the first *count
-    const int64_t q_tiles = ceil_div(m, kSimtTile);
-    int rc = ensure_qt(h, q_tiles * h->d_pad * kSimtTile);
-    if (rc) return rc;
-    const int64_t tps = ceil_div(h->n_tiles, fixup_splits(h));
-    const int64_t splits = ceil_div(h->n_tiles, tps);
-    rc = ensure_partials(h, splits * m);
-    if (rc) return rc;
-    count_launch(3);
-    gather_rows_tiles_kernel<<<grid_for(q_tiles * h->d_pad * kSimtTile, 256), 256, 0, s>>>(dQ, h->d, h->d_pad, idx,
-                                                                                           count, m, h->qt);
-    launch_simt(h, dim3((unsigned)(h->sm_count * 2)), s, m, tps, splits, count);
-    combine_scatter_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
-        h->part.sum, h->part.shift, m, (int)splits, idx, count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
-    STAG_CUDA_TRY(cudaGetLastError());
-    return 0;
+    return ensure_partials(h, ceil_div(h->n_tiles, tps) * m);
 }
 
 // Tile-transposed [tile][d_pad][64] back to row-major n x d.
@@ -543,6 +543,41 @@ int simt_points_rows(stag_kde *h, float *out, cudaStream_t s) {
 int launch_subtract(double *v, int64_t count, double one, cudaStream_t s) {
     count_launch();
     subtract_one_kernel<<<grid_for(count, 256), 256, 0, s>>>(v, count, one);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int simt_list_launch(const stag_kde *h, const float *xt, const float *qt, const int *kept, int64_t kstride,
+                     const int *kcount, const int *item_off, const int *n_groups, int seg, int per, double *part_sum,
+                     float *part_shift, cudaStream_t s) {
+    const float negc = (float)(-h->a * 1.4426950408889634);  // -a log2(e)
+    const dim3 grid((unsigned)(h->sm_count * 2));
+    count_launch();
+    if (h->d_pad <= kSimtKC)
+        kde_simt_f32_list_kernel<true, STAG_KDE_KERNEL_GAUSSIAN><<<grid, 256, 0, s>>>(
+            xt, h->n, h->n_tiles, qt, h->d_pad, negc, kept, kstride, kcount, item_off, n_groups, seg, per, part_sum,
+            part_shift);
+    else
+        kde_simt_f32_list_kernel<false, STAG_KDE_KERNEL_GAUSSIAN><<<grid, 256, 0, s>>>(
+            xt, h->n, h->n_tiles, qt, h->d_pad, negc, kept, kstride, kcount, item_off, n_groups, seg, per, part_sum,
+            part_shift);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int simt_gather_rows(const stag_kde *h, const float *dQ, const int *idx, const int *count, int64_t m_cap, float *qt,
+                     cudaStream_t s) {
+    count_launch();
+    gather_rows_tiles_kernel<<<grid_for(ceil_div(m_cap, kSimtTile) * h->d_pad * kSimtTile, 256), 256, 0, s>>>(
+        dQ, h->d, h->d_pad, idx, count, m_cap, qt);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
+int simt_tiles_from_rows(const stag_kde *h, const float *rows, float *out, cudaStream_t s) {
+    const int64_t total = h->n_tiles * h->d_pad * kSimtTile;
+    count_launch();
+    to_tiles_kernel<float><<<grid_for(total, 256), 256, 0, s>>>(rows, h->n, h->d, h->d_pad, h->n_tiles, out);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }

@@ -24,7 +24,7 @@
 // Kernel structure (persistent, one CTA per SM, warp-specialised):
 //   warp 0      TMA producer: per work unit the query tile's A planes (u_hi, u_lo, the
 //               constant column), per point tile the B planes (v_hi, v_lo, -g pieces)
-//               and a metadata block (R of the unit's 128 queries, the tile's RMS
+//               and a metadata block (R of the unit's 128 queries, the tile's
 //               radius) into rings of stages;
 //   warp 1      allocates TMEM; one thread issues 3 * K/16 + 1 MMAs per accumulator
 //               and commits. K = 16 ("ring"): four accumulators of 128 lanes x BN/2
@@ -71,12 +71,12 @@ struct TcData {
     __half *b_hi = nullptr, *b_lo = nullptr;  // [n_pad][Kp]
     __half *b_aug = nullptr;                  // [n_pad][16]: -g / (2 scale) in 3 FP16 pieces, then 0
     __half *a_aug = nullptr;                  // [128][16]: s_a, s_a, s_a, 0, ...
-    float *tinfo = nullptr;                   // [T][4]: RMS radius, max radius (rounded up to bound
+    float *tinfo = nullptr;                   // [T][4]: RMS radius, max radius rounded up to bound
+                                              //         FP32 distances (exponent bounds), max radius,
+                                              //         the error estimate's accumulation weight
                                               //         FP32 distances), 0, 0
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
     float *cg = nullptr;                      // [Kp]: global centre c_g
-    float *xs = nullptr;                      // [n][d]: the points in tile (k-d) order, FP32 row-major
-                                              //         (handles that recompute flagged queries)
     double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
     unsigned *vmax_bits = nullptr;            // max |x_k - c_t,k| (float bits)
     unsigned *xmax_bits = nullptr;            // max |x_k - c_g,k| (float bits)
@@ -90,10 +90,15 @@ struct TcData {
     int64_t rt_cap = 0;        // floats
     float *unorm = nullptr;    // [m_cap]: ||q - c_g|| per query
     int *qbad = nullptr;       // [m_cap]: query outside the FP16 range of the split
+    int *qflag = nullptr;      // [m_cap]: query handed to the FP32 recompute (this call)
     unsigned *ub = nullptr;    // [m_cap]: per-query exponent bound (order bits)
     int64_t unorm_cap = 0;
     double *part_w = nullptr;  // [splits][m]: contribution-weighted tile radius sums
     int64_t part_w_cap = 0;
+    float *xkt = nullptr;      // k-d ordered points in the plain form's tile-transposed layout
+                               // (the recompute of flagged queries)
+    void *gbuf = nullptr;      // grouped-recompute scratch (GroupScratch), sized for gbuf_m rows
+    int64_t gbuf_m = 0;
     int *fix_idx = nullptr;    // [m_cap]: queries handed to the plain form
     int *fix_count = nullptr;  // device counter
     int *err = nullptr;        // device error code (timeouts)
@@ -185,6 +190,7 @@ struct TcInst {
     const float *rowterm;  // [T][m_pad]
     const float *scales;   // device: scale_v, scale_u, kk, s_a
     const unsigned *ub;    // [m_pad]: per-query upper bound on every exponent (order bits)
+    const float *unorm;    // [m_pad]: ||q - c_g|| (the error estimate's split term)
     double *part_sum;      // [splits][m]
     float *part_shift;
     double *part_w;
@@ -240,7 +246,7 @@ struct RowState {
     float shift;
     float ksum;  // compensated sum of the tiles so far
     float kc;    // its compensation term
-    float w32;   // sum over tiles of (tile sum) * (tile RMS radius), same units as ksum
+    float w32;   // sum over tiles of (tile sum) * (tile's error weight), same units as ksum
 };
 
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
@@ -551,6 +557,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
         uint32_t tcount = 0, ucount = 0;  // point tiles and units this CTA has passed
         bool ok = true;
         RowState st{0.f, 0.f, 0.f, 0.f};
+        float au = 0.f;  // 2^-21 ||q - c_g|| of this row's query (set per unit)
         // This warp's columns of point tile number tc (CTA-wide count): wait for their
         // accumulator and the tile's row terms, sum the exponentials, release both, fold
         // the sum into the row state. Returns false on timeout or abort.
@@ -569,7 +576,9 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             ptx::tc_fence_after();
             const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
             const float nb = -(meta[row] + st.shift);
-            const float vrad = meta[BM];
+            // the tile's error-estimate weight for this row: the split term's RMS radius times
+            // 2^-21 ||u||, plus the accumulation term beta_K rho_t^2 (tinfo slot 3)
+            const float vw = fmaf(au, meta[BM], meta[BM + 3]);
             const uint64_t nb2 = pack2(nb, nb);
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + acc * C::ACC_COLS + (C::RING ? 0 : grp * WCOLS);
@@ -628,7 +637,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             unpack2(acc_b, s2, s3);
             const float ts = (s0 + s1) + (s2 + s3);
             kahan_add(st.ksum, st.kc, ts);
-            st.w32 = fmaf(ts, vrad, st.w32);
+            st.w32 = fmaf(ts, vw, st.w32);
             return true;
         };
         for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
@@ -652,6 +661,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             const int i_end = masked_end ? ntiles - 1 : ntiles;
             // the row's fixed shift: ceil of an upper bound on every exponent of the row
             st = RowState{ceilf(order_bits_to_float(I.ub[qt * BM + row])), 0.f, 0.f, 0.f};
+            au = 0x1p-21f * I.unorm[qt * BM + row];
             for (int i = i0; i < i_end && ok; i += STEP) ok = visit(std::false_type{}, kk2, tbase + i, WCOLS);
             if (ok && masked_end) ok = visit(std::true_type{}, kk2, tbase + ntiles - 1, vlast);
             tcount = tbase + ntiles;
@@ -839,8 +849,8 @@ __global__ void tc_split_points_kernel(const float *__restrict__ X, int64_t n, i
     }
 }
 
-// Per tile: the RMS distance of its points from the tile centre (used by the per-query
-// error estimate).
+// Per tile: the RMS and the largest distance of its points from the tile centre (the
+// per-query error estimate and the exponent bounds).
 __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
                                       const float *__restrict__ cent, float *__restrict__ tinfo) {
     __shared__ double red[128];
@@ -868,11 +878,17 @@ __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, in
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        tinfo[t * 4 + 0] = cnt > 0 ? (float)sqrt(red[0] / (double)cnt) : 0.f;  // RMS radius
+        // RMS radius: the error estimate's split term (the typical |v| of the tile)
+        tinfo[t * 4 + 0] = cnt > 0 ? (float)sqrt(red[0] / (double)cnt) : 0.f;
         // max radius, rounded up so that it bounds the FP32 distances too
         tinfo[t * 4 + 1] = cnt > 0 ? (float)(sqrt(redm[0]) * (1.0 + 1e-6)) : 0.f;
-        tinfo[t * 4 + 2] = 0.f;
-        tinfo[t * 4 + 3] = 0.f;
+        tinfo[t * 4 + 2] = cnt > 0 ? (float)sqrt(redm[0]) : 0.f;  // max radius
+        // the estimate's accumulation term: for a point near the query the FP32 accumulator
+        // carries about ||v||^2 + D_t . v before the point term cancels it, so its rounding
+        // error grows with the tile's largest ||v||^2 (large for a tile holding a few points
+        // of another cluster): 2^-23 sqrt(MMA steps) rho^2
+        const double steps = 3.0 * Kp / 16.0 + 1.0;
+        tinfo[t * 4 + 3] = cnt > 0 ? (float)(0x1p-23 * sqrt(steps) * redm[0]) : 0.f;
     }
 }
 
@@ -985,172 +1001,187 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
 // (with a 1e-5 relative slack on sqrt(R_t) for rounding), so LB = max_t lb_t bounds the
 // row's largest term from below, and a tile with ub_t < LB - 64 holds only terms below
 // 2^-64 of it: all of them together change the sum by less than n 2^-64 relative, and
-// the tile is skipped. The others are evaluated like the plain FP32 form: squared
-// distances by direct differences in FP32 chains of 16 coordinates whose sums are added
-// (the plain form's order, so the same d2 bits), one ex2 per pair, a per-lane
-// power-of-two shift raised when a term would pass 2^64, FP32 partial sums flushed to
-// FP64 every 16 terms, merged in FP64 in a fixed order. One block of 8 warps per flagged
-// query (grid-stride over the device count): tiles are bounded 32 at a time (one
-// ballot), warp w takes every 8th included tile of each group of 32, its lanes take two
-// points each (packed FP32x2 arithmetic) until the tile is done.
-constexpr int kPrunedWarps = 8;
+// the tile is skipped. The others are evaluated like the plain FP32 form.
 constexpr float kPruneLog2 = 64.f;
-constexpr int64_t kPrunedMaxD = 16;  // the per-query pruned pass serves d <= 16
 
-template <bool kVec4>
-__global__ void __launch_bounds__(32 * kPrunedWarps)
-tc_fixup_pruned_kernel(const float *__restrict__ Q, int d, const int *__restrict__ fix_idx,
-                       const int *__restrict__ fix_count, int64_t m_pad, const float *__restrict__ R,
-                       const float *__restrict__ tinfo, const float *__restrict__ xs, int64_t n, int64_t T, int BN,
-                       float c, double scale, double *__restrict__ out) {
-    extern __shared__ __align__(16) float sq[];  // [d] query, then the warps' partials
-    double *wsum = reinterpret_cast<double *>(sq + ((d + 3) & ~3));
-    float *wshift = reinterpret_cast<float *>(wsum + kPrunedWarps);
-    float *wlb = wshift + kPrunedWarps;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cnt = *fix_count;
-    const float sqc = sqrtf(c), negc = -c;
-    constexpr float kShiftInit = -0x1p100f, kGuard = 0x1p64f;
-    auto bounds = [&](int64_t t, int64_t q, float &ub, float &lb) {
-        const float r = sqrtf(R[t * m_pad + q]);
-        const float rho = sqc * tinfo[t * 4 + 1];
-        const float g = fmaxf(0.f, r * (1.f - 1e-5f) - rho);
-        const float h2 = r * (1.f + 1e-5f) + rho;
-        ub = -g * g;
-        lb = -h2 * h2;
-    };
-    float shift = kShiftInit, acc32 = 0.f;
-    double acc64 = 0.0;
-    int nacc = 0;
-    auto add_term = [&](float d2) {
-        float e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
-        if (!(fabsf(e) <= kGuard)) {
-            // first term, or one far above the current shift: move the shift up
-            const float s_new = fmaxf(ceilf(negc * d2), kShiftInit);
-            if (s_new > shift) {
-                const int de = cexp(shift - s_new);
-                acc32 = ldexpf(acc32, de);
-                acc64 = ldexp(acc64, de);
-                shift = s_new;
+// ---------------------------------------------------------------- grouped recompute
+// The flagged queries are recomputed in groups of 64 so that every point load serves 64
+// queries (the plain form's register-tiled kernel), while the tiles that cannot matter
+// are still skipped:
+//   (1) per flagged query: the bound LB of its largest exponent, its threshold LB - 64
+//       and, as sort key, the tile holding LB (unflagged queries get a key past every
+//       tile);
+//   (2) the queries stably sorted by that key from query order (k-d order: queries near
+//       the same points become neighbours; ties stay in query order, so the groups do not
+//       depend on the order in which the queries were flagged), the flagged ones gathered
+//       64 per group;
+//   (3) per group, the union of its members' kept tiles (ub_t >= threshold for at least
+//       one member);
+//   (4) the list kernel (kde_simt.cu) over each group's kept tiles, in segments of `seg`
+//       tiles;
+//   (5) per query, the FP64 combine of its group's segments.
+// A member evaluates the other members' tiles too: more terms than its own bound needs,
+// never fewer.
+__global__ void tc_group_key_kernel(const int *__restrict__ qflag, int64_t m, int64_t m_pad,
+                                    const float *__restrict__ R, const float *__restrict__ tinfo, int64_t T, float c,
+                                    uint64_t *__restrict__ key, uint32_t *__restrict__ val, float *__restrict__ thr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const float sqc = sqrtf(c);
+    // one warp per query, in query order (the stable sort then keeps that order within a
+    // tile, so the groups do not depend on the order in which queries were flagged)
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < m; q += warps) {
+        if (!qflag[q]) {  // not flagged: sorts after every flagged query
+            if (lane == 0) {
+                key[q] = (uint64_t)T;
+                val[q] = (uint32_t)q;
+                thr[q] = 0.f;
             }
-            e = kfn::term<STAG_KDE_KERNEL_GAUSSIAN>(negc, d2, shift);
+            continue;
         }
-        acc32 += e;
-        if (++nacc == 16) {
-            acc64 += (double)acc32;
-            acc32 = 0.f;
-            nacc = 0;
-        }
-    };
-    for (int64_t w = blockIdx.x; w < cnt; w += gridDim.x) {
-        const int64_t q = fix_idx[w];
-        for (int k = threadIdx.x; k < d; k += 32 * kPrunedWarps) sq[k] = Q[q * d + k];
-        // LB over all tiles
-        float lb_max = -INFINITY;
-        for (int64_t t = threadIdx.x; t < T; t += 32 * kPrunedWarps) {
-            float ub, lb;
-            bounds(t, q, ub, lb);
-            lb_max = fmaxf(lb_max, lb);
-        }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) lb_max = fmaxf(lb_max, __shfl_xor_sync(0xffffffffu, lb_max, o));
-        if (lane == 0) wlb[warp] = lb_max;
-        __syncthreads();
-        float thr = wlb[0];
-#pragma unroll
-        for (int i = 1; i < kPrunedWarps; ++i) thr = fmaxf(thr, wlb[i]);
-        thr -= kPruneLog2;
-        shift = kShiftInit;
-        acc32 = 0.f;
-        acc64 = 0.0;
-        nacc = 0;
-        for (int64_t t0 = 0; t0 < T; t0 += 32) {
-            bool keep = false;
-            if (t0 + lane < T) {
-                float ub, lb;
-                bounds(t0 + lane, q, ub, lb);
-                keep = ub >= thr;
-            }
-            unsigned mask = __ballot_sync(0xffffffffu, keep);
-            for (int rank = 0; mask; ++rank) {
-                const int64_t t = t0 + __ffs(mask) - 1;
-                mask &= mask - 1u;
-                if (rank % kPrunedWarps != warp) continue;
-                const int64_t p1 = min(n, (t + 1) * BN);
-                // two points per lane: p and p + 32 (the second repeats the first past the end)
-                for (int64_t p = t * BN + lane; p < p1; p += 64) {
-                    const bool two = p + 32 < p1;
-                    const float *xa = xs + p * d;
-                    const float *xb = xs + (two ? p + 32 : p) * d;
-                    uint64_t d2 = 0ull;  // {0.f, 0.f}
-                    for (int kb = 0; kb < d; kb += 16) {
-                        const int ke = min(d, kb + 16);
-                        uint64_t b2 = 0ull;
-                        if constexpr (kVec4) {
-                            for (int k = kb; k < ke; k += 4) {
-                                const float4 va = *reinterpret_cast<const float4 *>(xa + k);
-                                const float4 vb = *reinterpret_cast<const float4 *>(xb + k);
-                                const float4 qv = *reinterpret_cast<const float4 *>(sq + k);
-                                uint64_t df = f2::sub(f2::pack(qv.x, qv.x), f2::pack(va.x, vb.x));
-                                b2 = f2::fma(df, df, b2);
-                                df = f2::sub(f2::pack(qv.y, qv.y), f2::pack(va.y, vb.y));
-                                b2 = f2::fma(df, df, b2);
-                                df = f2::sub(f2::pack(qv.z, qv.z), f2::pack(va.z, vb.z));
-                                b2 = f2::fma(df, df, b2);
-                                df = f2::sub(f2::pack(qv.w, qv.w), f2::pack(va.w, vb.w));
-                                b2 = f2::fma(df, df, b2);
-                            }
-                        } else {
-                            for (int k = kb; k < ke; ++k) {
-                                const uint64_t df = f2::sub(f2::pack(sq[k], sq[k]), f2::pack(xa[k], xb[k]));
-                                b2 = f2::fma(df, df, b2);
-                            }
-                        }
-                        d2 = f2::add(d2, b2);
-                    }
-                    float da, db;
-                    f2::unpack(d2, da, db);
-                    add_term(da);
-                    if (two) add_term(db);
-                }
+        float best = -INFINITY;
+        int bt = (int)T;
+        for (int t = lane; t < (int)T; t += 32) {
+            const float h2 = sqrtf(R[(int64_t)t * m_pad + q]) * (1.f + 1e-5f) + sqc * tinfo[(int64_t)t * 4 + 1];
+            const float lb = -h2 * h2;
+            if (lb > best) {
+                best = lb;
+                bt = t;
             }
         }
-        acc64 += (double)acc32;
-        // merge the lanes, then the warps: common shift = the largest, fixed order
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            const double oa = __shfl_xor_sync(0xffffffffu, acc64, o);
-            const float os = __shfl_xor_sync(0xffffffffu, shift, o);
-            const float sm = fmaxf(shift, os);
-            acc64 = ldexp(acc64, cexp(shift - sm)) + ldexp(oa, cexp(os - sm));
-            shift = sm;
+        for (int o = 16; o; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
+            if (ob > best || (ob == best && ot < bt)) {
+                best = ob;
+                bt = ot;
+            }
         }
         if (lane == 0) {
-            wsum[warp] = acc64;
-            wshift[warp] = shift;
+            key[q] = (uint64_t)bt;
+            val[q] = (uint32_t)q;
+            thr[q] = best - kPruneLog2;
+        }
+    }
+}
+
+// Sorted position j -> query (order) and threshold; the number of groups.
+__global__ void tc_group_order_kernel(const uint32_t *__restrict__ val, const int *__restrict__ fix_count,
+                                      const float *__restrict__ thr, int *__restrict__ order,
+                                      float *__restrict__ thr_s, int *__restrict__ n_groups) {
+    const int cnt = *fix_count;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_groups = (cnt + 63) / 64;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+        order[j] = (int)val[j];
+        thr_s[j] = thr[val[j]];
+    }
+}
+
+// Per group (one block of 256 threads, grid-stride): the tiles some member may need, in
+// increasing order, into kept[g * T ..]; their number and the group's segment count.
+__global__ void __launch_bounds__(256)
+tc_group_keep_kernel(const int *__restrict__ order, const float *__restrict__ thr_s, const int *__restrict__ fix_count,
+                     const int *__restrict__ n_groups, int64_t m_pad, const float *__restrict__ R,
+                     const float *__restrict__ tinfo, int64_t T, float c, int seg, int *__restrict__ kept,
+                     int *__restrict__ kcount, int *__restrict__ items) {
+    __shared__ int sq[64];
+    __shared__ float sthr[64];
+    __shared__ int wcnt[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cnt = *fix_count, G = *n_groups;
+    const float sqc = sqrtf(c);
+    for (int g = blockIdx.x; g < G; g += gridDim.x) {
+        const int rows = min(64, cnt - g * 64);
+        __syncthreads();
+        if (threadIdx.x < rows) {
+            sq[threadIdx.x] = order[g * 64 + threadIdx.x];
+            sthr[threadIdx.x] = thr_s[g * 64 + threadIdx.x];
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            float sm = wshift[0];
-            for (int i = 1; i < kPrunedWarps; ++i) sm = fmaxf(sm, wshift[i]);
-            double tot = 0.0;
-            for (int i = 0; i < kPrunedWarps; ++i) tot += ldexp(wsum[i], cexp(wshift[i] - sm));
-            out[q] = ldexp(tot, cexp(sm)) * scale;
+        int base = 0;
+        for (int64_t t0 = 0; t0 < T; t0 += 256) {
+            const int64_t t = t0 + threadIdx.x;
+            bool keep = false;
+            if (t < T) {
+                const float rho = sqc * tinfo[t * 4 + 1];
+                for (int r = 0; r < rows && !keep; ++r) {
+                    const float gap = fmaxf(0.f, sqrtf(R[t * m_pad + sq[r]]) * (1.f - 1e-5f) - rho);
+                    keep = -gap * gap >= sthr[r];
+                }
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, keep);
+            if (lane == 0) wcnt[warp] = __popc(mask);
+            __syncthreads();
+            int off = base;
+            for (int w = 0; w < warp; ++w) off += wcnt[w];
+            if (keep) kept[(int64_t)g * T + off + __popc(mask & ((1u << lane) - 1u))] = (int)t;
+            for (int w = 0; w < 8; ++w) base += wcnt[w];
+            __syncthreads();
         }
-        __syncthreads();  // the query and the partials are free again
+        if (threadIdx.x == 0) {
+            kcount[g] = base;
+            items[g] = (base + seg - 1) / seg;
+        }
+    }
+}
+
+// Exclusive prefix sum of the groups' segment counts (one block; item_off has G + 1
+// entries).
+__global__ void __launch_bounds__(1024)
+tc_group_scan_kernel(const int *__restrict__ items, const int *__restrict__ n_groups, int *__restrict__ item_off) {
+    __shared__ int sdata[1024];
+    __shared__ int carry;
+    const int G = *n_groups;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < G; base += 1024) {
+        const int i = base + threadIdx.x;
+        sdata[threadIdx.x] = i < G ? items[i] : 0;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int v = threadIdx.x >= o ? sdata[threadIdx.x - o] : 0;
+            __syncthreads();
+            sdata[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (i < G) item_off[i + 1] = carry + sdata[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sdata[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) item_off[0] = 0;
+}
+
+// Per flagged query (sorted position j): the FP64 sum of its group's segment partials.
+__global__ void tc_group_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
+                                        const int *__restrict__ item_off, const int *__restrict__ order,
+                                        const int *__restrict__ fix_count, double scale, double *__restrict__ out) {
+    const int cnt = *fix_count;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = j / 64, r = j % 64;
+        const int w0 = item_off[g], w1 = item_off[g + 1];
+        float smax = -INFINITY;
+        for (int w = w0; w < w1; ++w) smax = fmaxf(smax, part_shift[(int64_t)w * 64 + r]);
+        double tot = 0.0;
+        for (int w = w0; w < w1; ++w) tot += ldexp(part_sum[(int64_t)w * 64 + r], cexp(part_shift[(int64_t)w * 64 + r] - smax));
+        out[order[j]] = w1 > w0 ? ldexp(tot, cexp(smax)) * scale : 0.0;
     }
 }
 
 // FP64 combine of the per-split partials (as kde_combine.cu) plus the per-query error
 // estimate of the tensor-core form,
-//     est = 2^-21 * a * ||q - c_g|| * (sum_t S_t r_t) / (sum_t S_t),
-// S_t the query's sum over tile t and r_t that tile's RMS radius. Queries with
-// est > thr (or an empty sum) are appended to fix_idx for the plain FP32 form.
+//     est = a * (sum_t S_t w_t) / (sum_t S_t),   w_t = 2^-21 ||q - c_g|| r_t + beta rho_t^2,
+// S_t the query's sum over tile t, r_t that tile's RMS radius (the split products' error
+// grows with ||q - c_g|| |x - c_t|), rho_t its largest radius and beta = 2^-23 sqrt(MMA
+// steps) (the FP32 accumulation's error grows with ||x - c_t||^2; see tc_tile_radius).
+// The epilogue accumulates sum_t S_t w_t. Queries with est > thr (or an empty sum) are
+// appended to fix_idx for the plain FP32 form.
 __global__ void tc_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
                                   const double *__restrict__ part_w, int64_t m, int splits, double scale,
-                                  const float *__restrict__ unorm, const int *__restrict__ qbad, double a,
+                                  const int *__restrict__ qbad, double a,
                                   double thr, double *__restrict__ out, int *__restrict__ fix_idx,
-                                  int *__restrict__ fix_count) {
+                                  int *__restrict__ fix_count, int *__restrict__ qflag) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         float smax = -INFINITY;
         for (int k = 0; k < splits; ++k) smax = fmaxf(smax, part_shift[(int64_t)k * m + j]);
@@ -1163,8 +1194,10 @@ __global__ void tc_combine_kernel(const double *__restrict__ part_sum, const flo
         out[j] = ldexp(tot, cexp(smax)) * scale;
         // tot is in units of 2^smax, a bound on every term: below 2^-40 the bound was too
         // loose for the fixed shift (terms under 2^-126 of it were flushed)
-        const double est = (tot >= 0x1p-40 && !qbad[j]) ? 0x1p-21 * a * (double)unorm[j] * (wt / tot) : INFINITY;
-        if (est > thr && fix_idx) fix_idx[atomicAdd(fix_count, 1)] = (int)j;
+        const double est = (tot >= 0x1p-40 && !qbad[j]) ? a * (wt / tot) : INFINITY;
+        const bool flag = est > thr && fix_idx;
+        if (flag) fix_idx[atomicAdd(fix_count, 1)] = (int)j;
+        if (qflag) qflag[j] = flag ? 1 : 0;
     }
 }
 
@@ -1279,7 +1312,7 @@ void tc_free(stag_kde *h) {
         cudaFree(tc->tinfo);
         cudaFree(tc->cent);
         cudaFree(tc->cg);
-        cudaFree(tc->xs);
+        cudaFree(tc->xkt);
         cudaFree(tc->tsum);
         cudaFree(tc->vmax_bits);
         cudaFree(tc->xmax_bits);
@@ -1294,6 +1327,8 @@ void tc_free(stag_kde *h) {
     cudaFree(tc->ub);
     cudaFree(tc->part_w);
     cudaFree(tc->fix_idx);
+    cudaFree(tc->qflag);
+    cudaFree(tc->gbuf);
     cudaFree(tc->fix_count);
     cudaFree(tc->err);
     if (tc->err_host) cudaFreeHost(tc->err_host);
@@ -1320,7 +1355,7 @@ int tc_make_view(const stag_kde *base, stag_kde *view) {
     tc->tinfo = b->tinfo;
     tc->cent = b->cent;
     tc->cg = b->cg;
-    tc->xs = b->xs;
+    tc->xkt = b->xkt;
     tc->tsum = b->tsum;
     tc->vmax_bits = b->vmax_bits;
     tc->xmax_bits = b->xmax_bits;
@@ -1352,10 +1387,12 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     STAG_CUDA_TRY(dev_malloc(&tc->tinfo, tc->T * 4 * sizeof(float)));
     STAG_CUDA_TRY(dev_malloc(&tc->cent, tc->T * Kp * sizeof(float)));
     STAG_CUDA_TRY(dev_malloc(&tc->cg, Kp * sizeof(float)));
-    if (h->tc_check && h->d <= kPrunedMaxD) {
-        // only the pruned recompute of flagged queries reads the ordered FP32 points
-        STAG_CUDA_TRY(dev_malloc(&tc->xs, h->n * h->d * sizeof(float)));
-        STAG_CUDA_TRY(cudaMemcpyAsync(tc->xs, dX, h->n * h->d * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    // the recompute of flagged queries reads the points in tile (k-d) order, in the plain
+    // form's tile-transposed layout
+    if (h->tc_check) {
+        STAG_CUDA_TRY(dev_malloc(&tc->xkt, h->n_tiles * h->d_pad * kSimtTile * sizeof(float)));
+        int rc0 = simt_tiles_from_rows(h, dX, tc->xkt, s);
+        if (rc0) return rc0;
     }
     STAG_CUDA_TRY(dev_malloc(&tc->tsum, tc->T * Kp * sizeof(double)));
     STAG_CUDA_TRY(dev_malloc(&tc->vmax_bits, sizeof(unsigned)));
@@ -1387,6 +1424,50 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     return rc;
 }
 
+// Carving of the grouped-recompute scratch for up to m query rows.
+struct GroupScratch {
+    uint64_t *key, *ktmp;
+    uint32_t *val, *vtmp, *hist;
+    float *thr, *thr_s;
+    int *order, *kept, *kcount, *items, *item_off, *n_groups;
+    double *psum;
+    float *pshift;
+};
+
+// Kept point tiles per work item: at least eight 64-point tiles (the per-item set-up is
+// then amortised), and at most 64 items per group.
+static int group_seg(int64_t T, int BN) { return (int)std::max<int64_t>(8 * 64 / BN, ceil_div(T, 64)); }
+
+static int64_t group_scratch_bytes(int64_t m, int64_t T, int BN, GroupScratch *gs, void *base) {
+    const int64_t G = ceil_div(std::max<int64_t>(m, 1), 64);
+    const int64_t items = G * ceil_div(T, group_seg(T, BN));  // at most 64 segments per group
+    int64_t off = 0;
+    auto take = [&](int64_t bytes) {
+        const int64_t o = off;
+        off += round_up(bytes, 256);
+        return static_cast<char *>(base) + o;
+    };
+    const int64_t mm = std::max<int64_t>(m, 1);
+    GroupScratch g;
+    g.key = (uint64_t *)take(mm * 8);
+    g.ktmp = (uint64_t *)take(mm * 8);
+    g.val = (uint32_t *)take(mm * 4);
+    g.vtmp = (uint32_t *)take(mm * 4);
+    g.hist = (uint32_t *)take(radix_sort_hist_entries(mm) * 4);
+    g.thr = (float *)take(mm * 4);
+    g.thr_s = (float *)take(mm * 4);
+    g.order = (int *)take(mm * 4);
+    g.kept = (int *)take(G * T * 4);
+    g.kcount = (int *)take(G * 4);
+    g.items = (int *)take(G * 4);
+    g.item_off = (int *)take((G + 1) * 4);
+    g.n_groups = (int *)take(4);
+    g.psum = (double *)take(items * 64 * 8);
+    g.pshift = (float *)take(items * 64 * 4);
+    if (gs) *gs = g;
+    return off;
+}
+
 static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
     TcData *tc = h->tc;
     const int Kp = tc->Kp;
@@ -1408,6 +1489,8 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         cudaFree(tc->qbad);
         cudaFree(tc->ub);
         cudaFree(tc->fix_idx);
+        cudaFree(tc->qflag);
+        tc->qflag = nullptr;
         tc->unorm = nullptr;
         tc->qbad = nullptr;
         tc->ub = nullptr;
@@ -1417,6 +1500,7 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         STAG_CUDA_TRY(dev_malloc(&tc->qbad, m_pad * sizeof(int)));
         STAG_CUDA_TRY(dev_malloc(&tc->ub, m_pad * sizeof(unsigned)));
         STAG_CUDA_TRY(dev_malloc(&tc->fix_idx, m_pad * sizeof(int)));
+        STAG_CUDA_TRY(dev_malloc(&tc->qflag, m_pad * sizeof(int)));
         tc->unorm_cap = m_pad;
     }
     if (!tc->fix_count) STAG_CUDA_TRY(dev_malloc(&tc->fix_count, sizeof(int)));
@@ -1457,8 +1541,18 @@ int tc_reserve(stag_kde *h, int64_t m, int tiles_per_unit) {
     if (rc) return rc;
     int64_t qt, sp, tps;
     plan_units(h, m, tiles_per_unit, &qt, &sp, &tps);
-    // above d = 16 flagged queries are recomputed by the plain form (tiled copy, partials)
-    if (h->d > kPrunedMaxD) rc = simt_reserve(h, m);
+    // the grouped recompute needs its scratch and gathered query tiles
+    if (h->tc_check) {
+        if (tc->gbuf_m < m) {
+            ++h->scratch_epoch;
+            cudaFree(tc->gbuf);
+            tc->gbuf = nullptr;
+            tc->gbuf_m = 0;
+            STAG_CUDA_TRY(dev_malloc(&tc->gbuf, group_scratch_bytes(m, tc->T, tc->BN, nullptr, nullptr)));
+            tc->gbuf_m = m;
+        }
+        rc = ensure_qt(h, ceil_div(m, kSimtTile) * h->d_pad * kSimtTile);
+    }
     if (!rc) rc = ensure_partials(h, sp * m);
     if (rc) return rc;
     if (tc->part_w_cap < sp * m) {
@@ -1481,7 +1575,9 @@ static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     STAG_CUDA_TRY(cudaMemsetAsync(tc->qbad, 0, m_pad * sizeof(int), s));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->ub, 0, m_pad * sizeof(unsigned), s));
     count_launch(1);
-    const int tpb = 64;
+    // tiles per block: 64, fewer when that leaves under ~4 blocks per SM (small batches)
+    int tpb = 64;
+    while (tpb > 8 && (m_pad / BM) * ceil_div(tc->T, tpb) < 4 * (int64_t)h->sm_count) tpb /= 2;
     dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
     switch (Kp) {
 #define STAG_ROWTERM(KPV)                                                                                          \
@@ -1514,6 +1610,7 @@ static void fill_inst(const stag_kde *h, int64_t m, int64_t q_tiles, int64_t spl
     I->rowterm = tc->rowterm;
     I->scales = tc->scales;
     I->ub = tc->ub;
+    I->unorm = tc->unorm;
     I->part_sum = h->part.sum;
     I->part_shift = h->part.shift;
     I->part_w = tc->part_w;
@@ -1527,36 +1624,59 @@ static void fill_inst(const stag_kde *h, int64_t m, int64_t q_tiles, int64_t spl
     I->units = q_tiles * splits;
 }
 
+// Grouped recompute of the flagged queries, all on stream s.
+static int tc_fixup_grouped(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s) {
+    TcData *tc = h->tc;
+    GroupScratch g;
+    group_scratch_bytes(m, tc->T, tc->BN, &g, tc->gbuf);
+    const int64_t m_pad = round_up(m, BM);
+    const float c = (float)(h->a * 1.4426950408889634);
+    const int seg = group_seg(tc->T, tc->BN);
+    const int per = tc->BN / kSimtTile;
+    count_launch(3);
+    tc_group_key_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 8), (int64_t)h->sm_count * 16), 256, 0, s>>>(
+        tc->qflag, m, m_pad, tc->rowterm, tc->tinfo, tc->T, c, g.key, g.val, g.thr);
+    STAG_CUDA_TRY(cudaGetLastError());
+    int bits = 1;  // tile indices and the sentinel T
+    while (((int64_t)1 << bits) <= tc->T) ++bits;
+    int rc = radix_sort_pairs(g.key, g.val, g.ktmp, g.vtmp, g.hist, m, bits, s);
+    if (rc) return rc;
+    tc_group_order_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1024), 256, 0, s>>>(
+        g.val, tc->fix_count, g.thr, g.order, g.thr_s, g.n_groups);
+    rc = simt_gather_rows(h, dQ, g.order, tc->fix_count, m, h->qt, s);
+    if (rc) return rc;
+    tc_group_keep_kernel<<<(unsigned)(h->sm_count * 4), 256, 0, s>>>(g.order, g.thr_s, tc->fix_count, g.n_groups,
+                                                                      m_pad, tc->rowterm, tc->tinfo, tc->T, c, seg,
+                                                                      g.kept, g.kcount, g.items);
+    count_launch();
+    tc_group_scan_kernel<<<1, 1024, 0, s>>>(g.items, g.n_groups, g.item_off);
+    STAG_CUDA_TRY(cudaGetLastError());
+    rc = simt_list_launch(h, tc->xkt, h->qt, g.kept, tc->T, g.kcount, g.item_off, g.n_groups, seg, per, g.psum,
+                          g.pshift, s);
+    if (rc) return rc;
+    count_launch();
+    tc_group_combine_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1024), 256, 0, s>>>(
+        g.psum, g.pshift, g.item_off, g.order, tc->fix_count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 // FP64 combine with the per-query error estimate, then the FP32 recompute of the flagged
-// queries over the tiles that can matter (tc_fixup_pruned_kernel).
+// queries over the tiles that can matter (tc_fixup_grouped).
 static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
     TcData *tc = h->tc;
     const bool check = h->tc_check;
     if (check) STAG_CUDA_TRY(cudaMemsetAsync(tc->fix_count, 0, sizeof(int), s));
     count_launch();
     tc_combine_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
-        h->part.sum, h->part.shift, tc->part_w, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0, tc->unorm,
-        tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count);
+        h->part.sum, h->part.shift, tc->part_w, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
+        tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count,
+        check ? tc->qflag : nullptr);
     STAG_CUDA_TRY(cudaGetLastError());
     if (!check) return 0;
-    // Above d = 16 the per-query pass would re-read its kept tiles once per flagged query;
-    // the plain form's tiled kernel over all points shares each load across 64 queries.
-    if (h->d > kPrunedMaxD) return simt_fixup_rows(h, dQ, m, tc->fix_idx, tc->fix_count, dOut, s);
-    const unsigned grid = (unsigned)(h->sm_count * 8);
-    const size_t smem = (size_t)(((h->d + 3) & ~3) * sizeof(float) + kPrunedWarps * (sizeof(double) + 2 * sizeof(float)));
-    const float c = (float)(h->a * 1.4426950408889634);
-    const double scale = h->normalise ? 1.0 / (double)h->n : 1.0;
-    count_launch();
-    if (h->d % 4 == 0)
-        tc_fixup_pruned_kernel<true><<<grid, 32 * kPrunedWarps, smem, s>>>(
-            dQ, (int)h->d, tc->fix_idx, tc->fix_count, round_up(m, BM), tc->rowterm, tc->tinfo, tc->xs, h->n, tc->T,
-            tc->BN, c, scale, dOut);
-    else
-        tc_fixup_pruned_kernel<false><<<grid, 32 * kPrunedWarps, smem, s>>>(
-            dQ, (int)h->d, tc->fix_idx, tc->fix_count, round_up(m, BM), tc->rowterm, tc->tinfo, tc->xs, h->n, tc->T,
-            tc->BN, c, scale, dOut);
-    STAG_CUDA_TRY(cudaGetLastError());
-    return 0;
+    // groups of 64 flagged queries share every point load (a per-query pass would re-read
+    // its kept tiles once per query)
+    return tc_fixup_grouped(h, dQ, m, dOut, s);
 }
 
 int tc_operand_width(const stag_kde *h) { return h->tc ? h->tc->Kp : 0; }

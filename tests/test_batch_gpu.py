@@ -91,3 +91,48 @@ def test_autotune_keeps_results(lib):
         k.autotune(torch.from_numpy(Q).cuda())
         after = k.query(Q)
     assert oracle.rel_err(after, before).max() <= TOL
+
+
+@pytest.mark.slow
+def test_full_256_instance_workload_every_instance_sampled(lib):
+    # the batched workload at its full size (256 instances, n log-U[1e3, 2e5], m
+    # log-U[64, 8192], d cycling 8, 32, 128, a U[0.01, 1]) in one graph-replayed call, in
+    # the configuration the benchmark times: 16 sampled queries of EVERY instance against
+    # the oracle, at the tensor-core form's tolerance for their condition numbers
+    import torch
+    import bench
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE, query_batch
+    from tests._common import tol_tc
+    inst = bench.build_batched(256)
+    kdes = [ExactGaussianKDE(X, a) for X, _, a in inst]
+    Qs = [torch.from_numpy(Q).cuda() for _, Q, _ in inst]
+    outs = [torch.empty(q.shape[0], dtype=torch.float64, device="cuda") for q in Qs]
+    query_batch(kdes, Qs, outs)
+    query_batch(kdes, Qs, outs)  # the replay
+    torch.cuda.synchronize()
+    worst = 0.0
+    for i, (X, Q, a) in enumerate(inst):
+        idx = np.linspace(0, len(Q) - 1, min(16, len(Q))).astype(int)
+        logk, _, kappa = oracle.kde_log(X, Q[idx], a)
+        err = oracle.rel_err(outs[i].cpu().numpy()[idx], np.exp(logk))
+        assert np.all(err <= tol_tc(kappa, X.shape[1])), (i, X.shape, a, float(err.max()))
+        worst = max(worst, float(err.max()))
+    assert worst <= 1e-4  # every instance's kappa stays below 400 here
+    for k in kdes:
+        k.close()
+
+
+def test_tc_estimate_flags_queries_near_outlying_points_of_a_tile(lib):
+    # one instance of the batched workload (index 95: n = 3317, d = 128, a = 0.061) whose
+    # k-d tiles mix points of two mixture components: a query's dominant terms then come
+    # from points far from their tile's centre, and the error estimate must charge them
+    # with the tile's largest radius, not its typical one
+    import bench
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE
+    from tests._common import tol_tc
+    X, Q, a = bench.build_batched(96)[95]
+    with ExactGaussianKDE(X, a, form="tc") as kde:
+        got = kde.query(Q)
+    logk, _, kappa = oracle.kde_log(X, Q, a)
+    err = oracle.rel_err(got, np.exp(logk))
+    assert np.all(err <= tol_tc(kappa, X.shape[1])), float(err.max())

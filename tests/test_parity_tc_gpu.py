@@ -215,7 +215,7 @@ def test_single_instance_d16_workload_every_query(K, single_d16, form):
         tol = tol_tc(kappa, 16) if form == "tc" else tol_f32(kappa, 16)
         assert np.all(err <= tol), (a, float(err.max()), int(np.sum(err > tol)))
         if form == "tc":
-            assert redo <= 0.02 * len(Q), (a, redo)
+            assert redo <= 0.05 * len(Q), (a, redo)
 
 
 @pytest.mark.slow
@@ -228,3 +228,25 @@ def test_tc_large_d64_workload_1000_sampled_queries(K):
     idx = np.linspace(0, len(Q) - 1, 1000).astype(int)
     logk, _, kappa = oracle.kde_log(X, Q[idx], a)
     assert np.all(oracle.rel_err(got[idx], np.exp(logk)) <= tol_tc(kappa, 64))
+
+
+@pytest.mark.parametrize("d,n", [(5, 7001), (16, 20011), (33, 10007), (64, 9001), (100, 5003), (128, 12345)])
+def test_tc_grouped_recompute_of_flagged_queries(K, d, n):
+    # 10-component mixtures (means U[-10, 10]^d, std 1) at bandwidths whose condition
+    # numbers send most queries to the FP32 recompute, which runs in groups of 64 sorted
+    # queries over the union of their kept tiles. Ragged n leaves the last point tile
+    # partial in both the 128/256-point and the 64-point tilings.
+    from paper_2407_07096_gb300 import datagen as G
+    from tests._common import tol_tc
+    mix = G.make_mixture(d, 10, d, -10.0, 10.0, 1.0)
+    X, Q = G.sample(mix, d, n, "data"), G.sample(mix, d, 900, "query")
+    a = 60.0 / (2.0 * d)
+    with K(X, a, form="tc") as kde:
+        got = kde.query(Q)
+        redo = kde.last_recomputed()
+        again = kde.query(Q)
+    logk, _, kappa = oracle.kde_log(X, Q, a)
+    assert redo > (300 if d >= 16 else 100)
+    assert np.array_equal(got, again)
+    err = oracle.rel_err(got, np.exp(logk))
+    assert np.all(err <= tol_tc(kappa, d)), err.max()
