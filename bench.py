@@ -310,18 +310,34 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+KERNEL_REGION = ("__global__ void __launch_bounds__(64 + 128 * EG, 1)",
+                 "// ------------------------------------------------------------------ prep kernels")
+
+
+def kernel_digest(path):
+    """SHA-256 of the tensor-core kernel's own source (from its declaration to the prep
+    kernels that follow it) and of the inline-PTX and packed-math headers it includes:
+    the DRAM traffic of a capture stays valid while these are unchanged."""
+    import hashlib
+    src = open(os.path.join(ROOT, path)).read()
+    a, b = src.index(KERNEL_REGION[0]), src.index(KERNEL_REGION[1])
+    h = hashlib.sha256(src[a:b].encode())
+    for hdr in ("sm100_ptx.cuh", "f32x2.cuh"):
+        with open(os.path.join(os.path.dirname(os.path.join(ROOT, path)), hdr), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def recorded_traffic(workload, form):
     """DRAM bytes per launch of the dominant kernel from the committed ncu capture, if the
-    kernel's source is unchanged since (same SHA-256); otherwise None."""
-    import hashlib
+    kernel's source is unchanged since (same digest); otherwise None."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(workload)
         if not rec or form != "tc":
             return None
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != rec["source_sha256"]:
-                return None
+        if kernel_digest(rec["source"]) != rec["kernel_sha256"]:
+            return None
         return rec["dram_bytes_per_launch"]
     except (OSError, ValueError, KeyError):
         return None

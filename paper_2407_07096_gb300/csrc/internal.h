@@ -165,8 +165,10 @@ int launch_combine(const double *part_sum, const float *part_shift, int64_t m, i
 // Stable LSD radix sort of (64-bit key, 32-bit value) pairs by key bits [0, bits); the
 // result ends in (keys, vals); hist holds radix_sort_hist_entries(n) entries (the digit
 // histogram, 256 per block of 4096 keys, and the totals of its scan chunks).
+// With dcount (device memory) only the first min(n, *dcount) entries are sorted (the
+// buffers are still sized for n; the rest is left as it is).
 int radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t *hist, int64_t n,
-                     int bits, cudaStream_t s);
+                     int bits, cudaStream_t s, const int *dcount = nullptr);
 inline int64_t radix_sort_blocks(int64_t n) { return ceil_div(n, 4096); }
 inline int64_t radix_sort_hist_entries(int64_t n) {
     const int64_t e = 256 * radix_sort_blocks(n);

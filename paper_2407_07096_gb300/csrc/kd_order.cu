@@ -50,13 +50,18 @@ __device__ __forceinline__ uint32_t seg_id(int64_t t, int64_t T, int level) {
 }
 
 // ------------------------------------------------------------------ radix sort
-__global__ void rs_hist_kernel(const uint64_t *__restrict__ keys, int64_t n, int shift, int nblocks,
-                               uint32_t *__restrict__ hist) {
+// dcount (device, optional): only the first min(n, *dcount) entries take part
+__device__ __forceinline__ int64_t rs_count(int64_t n, const int *dcount) {
+    return dcount ? min(n, (int64_t)max(0, *dcount)) : n;
+}
+
+__global__ void rs_hist_kernel(const uint64_t *__restrict__ keys, int64_t n, const int *__restrict__ dcount, int shift,
+                               int nblocks, uint32_t *__restrict__ hist) {
     __shared__ uint32_t h[256];
     h[threadIdx.x] = 0;
     __syncthreads();
     const int64_t b0 = (int64_t)blockIdx.x * kRsChunk;
-    const int64_t b1 = min(n, b0 + kRsChunk);
+    const int64_t b1 = min(rs_count(n, dcount), b0 + kRsChunk);
     for (int64_t i = b0 + threadIdx.x; i < b1; i += kRsThreads) atomicAdd(&h[(keys[i] >> shift) & 255u], 1u);
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -131,8 +136,8 @@ __global__ void rs_scan_kernel(uint32_t *__restrict__ a, int64_t count) {
 // match masks and per-warp digit counts.
 __global__ void __launch_bounds__(kRsThreads)
 rs_scatter_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-                  uint32_t *__restrict__ vout, int64_t n, int shift, int nblocks, const uint32_t *__restrict__ hist,
-                  const uint32_t *__restrict__ part) {
+                  uint32_t *__restrict__ vout, int64_t n, const int *__restrict__ dcount, int shift, int nblocks,
+                  const uint32_t *__restrict__ hist, const uint32_t *__restrict__ part) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t cnt[kRsThreads / 32][256];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -141,7 +146,7 @@ rs_scatter_kernel(const uint64_t *__restrict__ kin, const uint32_t *__restrict__
     for (int w = 0; w < kRsThreads / 32; ++w) cnt[w][threadIdx.x] = 0;
     __syncthreads();
     const int64_t b0 = (int64_t)blockIdx.x * kRsChunk;
-    const int64_t b1 = min(n, b0 + kRsChunk);
+    const int64_t b1 = min(rs_count(n, dcount), b0 + kRsChunk);
     for (int64_t r0 = b0; r0 < b1; r0 += kRsThreads) {
         const int64_t i = r0 + threadIdx.x;
         const bool valid = i < b1;
@@ -256,7 +261,7 @@ int grid_of(int64_t total, int threads) { return (int)std::min<int64_t>(ceil_div
 // Stable sort of (keys, vals) by key bits [0, bits), ping-ponging with the tmp buffers;
 // the result ends in (keys, vals). hist needs radix_sort_hist_entries(n) entries.
 int radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *vtmp, uint32_t *hist, int64_t n,
-                     int bits, cudaStream_t s) {
+                     int bits, cudaStream_t s, const int *dcount) {
     const int nblocks = (int)ceil_div(n, kRsChunk);
     const int64_t entries = (int64_t)256 * nblocks;
     const int64_t chunks = ceil_div(entries, kScanChunk);
@@ -266,10 +271,10 @@ int radix_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *ktmp, uint32_t *v
     int passes = 0;
     for (int shift = 0; shift < bits; shift += 8, ++passes) {
         count_launch(4);
-        rs_hist_kernel<<<nblocks, 256, 0, s>>>(ka, n, shift, nblocks, hist);
+        rs_hist_kernel<<<nblocks, 256, 0, s>>>(ka, n, dcount, shift, nblocks, hist);
         rs_scan_chunks_kernel<<<(unsigned)chunks, kScanThreads, 0, s>>>(hist, entries, part);
         rs_scan_kernel<<<1, 1024, 0, s>>>(part, chunks);
-        rs_scatter_kernel<<<nblocks, kRsThreads, 0, s>>>(ka, va, kb, vb, n, shift, nblocks, hist, part);
+        rs_scatter_kernel<<<nblocks, kRsThreads, 0, s>>>(ka, va, kb, vb, n, dcount, shift, nblocks, hist, part);
         std::swap(ka, kb);
         std::swap(va, vb);
     }

@@ -90,7 +90,6 @@ struct TcData {
     int64_t rt_cap = 0;        // floats
     float *unorm = nullptr;    // [m_cap]: ||q - c_g|| per query
     int *qbad = nullptr;       // [m_cap]: query outside the FP16 range of the split
-    int *qflag = nullptr;      // [m_cap]: query handed to the FP32 recompute (this call)
     unsigned *ub = nullptr;    // [m_cap]: per-query exponent bound (order bits)
     int64_t unorm_cap = 0;
     double *part_w = nullptr;  // [splits][m]: contribution-weighted tile radius sums
@@ -576,9 +575,9 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             ptx::tc_fence_after();
             const float *meta = reinterpret_cast<const float *>(smem + C::OFF_META + ms * C::META_STRIDE);
             const float nb = -(meta[row] + st.shift);
-            // the tile's error-estimate weight for this row: the split term's RMS radius times
-            // 2^-21 ||u||, plus the accumulation term beta_K rho_t^2 (tinfo slot 3)
-            const float vw = fmaf(au, meta[BM], meta[BM + 3]);
+            // the tile's error-estimate weight for this row: the split term (RMS radius times
+            // 2^-21 ||u||) or, where larger, the accumulation term beta_K rho_t^2 (slot 3)
+            const float vw = fmaxf(au * meta[BM], meta[BM + 3]);
             const uint64_t nb2 = pack2(nb, nb);
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + acc * C::ACC_COLS + (C::RING ? 0 : grp * WCOLS);
@@ -1008,13 +1007,12 @@ constexpr float kPruneLog2 = 64.f;
 // The flagged queries are recomputed in groups of 64 so that every point load serves 64
 // queries (the plain form's register-tiled kernel), while the tiles that cannot matter
 // are still skipped:
-//   (1) per flagged query: the bound LB of its largest exponent, its threshold LB - 64
-//       and, as sort key, the tile holding LB (unflagged queries get a key past every
-//       tile);
-//   (2) the queries stably sorted by that key from query order (k-d order: queries near
-//       the same points become neighbours; ties stay in query order, so the groups do not
-//       depend on the order in which the queries were flagged), the flagged ones gathered
-//       64 per group;
+//   (1) the combine kernel flags queries and counts them per block; a scan and an ordered
+//       compaction list the flagged queries in query order, each with the bound LB of its
+//       largest exponent, its threshold LB - 64 and, as sort key, the tile holding LB;
+//   (2) a stable sort by that tile (k-d order: queries near the same points become
+//       neighbours; stable on an ordered input, so the groups are deterministic; it visits
+//       only the flagged entries) and the gather of the sorted queries, 64 per group;
 //   (3) per group, the union of its members' kept tiles (ub_t >= threshold for at least
 //       one member);
 //   (4) the list kernel (kde_simt.cu) over each group's kept tiles, in segments of `seg`
@@ -1022,81 +1020,97 @@ constexpr float kPruneLog2 = 64.f;
 //   (5) per query, the FP64 combine of its group's segments.
 // A member evaluates the other members' tiles too: more terms than its own bound needs,
 // never fewer.
-__global__ void tc_group_key_kernel(const int *__restrict__ qflag, int64_t m, int64_t m_pad,
-                                    const float *__restrict__ R, const float *__restrict__ tinfo, int64_t T, float c,
-                                    uint64_t *__restrict__ key, uint32_t *__restrict__ val, float *__restrict__ thr) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const float sqc = sqrtf(c);
-    // one warp per query, in query order (the stable sort then keeps that order within a
-    // tile, so the groups do not depend on the order in which queries were flagged)
-    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < m; q += warps) {
-        if (!qflag[q]) {  // not flagged: sorts after every flagged query
-            if (lane == 0) {
-                key[q] = (uint64_t)T;
-                val[q] = (uint32_t)q;
-                thr[q] = 0.f;
-            }
-            continue;
+// Exclusive prefix sum (one block): off[0..n] from in[0..n), n = *n_dev if given, else
+// the flagged queries' group count ceil(*cnt_dev / 64) if given, else n_host; the total
+// also goes to *total_out if given.
+__global__ void __launch_bounds__(1024)
+tc_scan_kernel(const int *__restrict__ in, const int *__restrict__ cnt_dev, int n_host, int *__restrict__ off,
+               int *__restrict__ total_out) {
+    __shared__ int sdata[1024];
+    __shared__ int carry;
+    const int n = cnt_dev ? (*cnt_dev + 63) / 64 : n_host;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + threadIdx.x;
+        sdata[threadIdx.x] = i < n ? in[i] : 0;
+        __syncthreads();
+        for (int o = 1; o < 1024; o <<= 1) {
+            const int v = threadIdx.x >= o ? sdata[threadIdx.x - o] : 0;
+            __syncthreads();
+            sdata[threadIdx.x] += v;
+            __syncthreads();
         }
-        float best = -INFINITY;
-        int bt = (int)T;
-        for (int t = lane; t < (int)T; t += 32) {
-            const float h2 = sqrtf(R[(int64_t)t * m_pad + q]) * (1.f + 1e-5f) + sqc * tinfo[(int64_t)t * 4 + 1];
+        if (i < n) off[i + 1] = carry + sdata[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += sdata[1023];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        off[0] = 0;
+        if (total_out) *total_out = carry;
+    }
+}
+
+// The flagged queries in query order (block b's flagged queries start at boff[b]; inside
+// a block, by warp, then lane), each with the tile holding the lower bound LB of its
+// largest exponent as sort key, and its threshold LB - 64. One thread per query: the row
+// terms of 32 consecutive queries are read together, tile by tile.
+__global__ void __launch_bounds__(256)
+tc_flag_compact_kernel(const int *__restrict__ qflag, const int *__restrict__ boff, int64_t m, int64_t m_pad,
+                       const float *__restrict__ R, const float *__restrict__ tinfo, int64_t T, float c,
+                       int *__restrict__ fix_idx, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+                       float *__restrict__ thr) {
+    __shared__ int wcnt[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool flag = j < m && qflag[j];
+    const unsigned mask = __ballot_sync(0xffffffffu, flag);
+    if (lane == 0) wcnt[warp] = __popc(mask);
+    __syncthreads();
+    if (!mask) return;
+    int w = boff[blockIdx.x] + __popc(mask & ((1u << lane) - 1u));
+    for (int k = 0; k < warp; ++k) w += wcnt[k];
+    const float sqc = sqrtf(c);
+    float best = -INFINITY;
+    int bt = 0;
+    if (flag) {
+        for (int t = 0; t < (int)T; ++t) {
+            const float h2 = sqrtf(R[(int64_t)t * m_pad + j]) * (1.f + 1e-5f) + sqc * tinfo[(int64_t)t * 4 + 1];
             const float lb = -h2 * h2;
-            if (lb > best) {
+            if (lb > best) {  // ties keep the smaller tile
                 best = lb;
                 bt = t;
             }
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int ot = __shfl_xor_sync(0xffffffffu, bt, o);
-            if (ob > best || (ob == best && ot < bt)) {
-                best = ob;
-                bt = ot;
-            }
-        }
-        if (lane == 0) {
-            key[q] = (uint64_t)bt;
-            val[q] = (uint32_t)q;
-            thr[q] = best - kPruneLog2;
-        }
-    }
-}
-
-// Sorted position j -> query (order) and threshold; the number of groups.
-__global__ void tc_group_order_kernel(const uint32_t *__restrict__ val, const int *__restrict__ fix_count,
-                                      const float *__restrict__ thr, int *__restrict__ order,
-                                      float *__restrict__ thr_s, int *__restrict__ n_groups) {
-    const int cnt = *fix_count;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *n_groups = (cnt + 63) / 64;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
-        order[j] = (int)val[j];
-        thr_s[j] = thr[val[j]];
+        fix_idx[w] = (int)j;
+        key[w] = (uint64_t)bt;
+        val[w] = (uint32_t)j;
+        thr[j] = best - kPruneLog2;
     }
 }
 
 // Per group (one block of 256 threads, grid-stride): the tiles some member may need, in
 // increasing order, into kept[g * T ..]; their number and the group's segment count.
 __global__ void __launch_bounds__(256)
-tc_group_keep_kernel(const int *__restrict__ order, const float *__restrict__ thr_s, const int *__restrict__ fix_count,
-                     const int *__restrict__ n_groups, int64_t m_pad, const float *__restrict__ R,
-                     const float *__restrict__ tinfo, int64_t T, float c, int seg, int *__restrict__ kept,
-                     int *__restrict__ kcount, int *__restrict__ items) {
+tc_group_keep_kernel(const uint32_t *__restrict__ order, const float *__restrict__ thr,
+                     const int *__restrict__ fix_count, int *__restrict__ n_groups, int64_t m_pad,
+                     const float *__restrict__ R, const float *__restrict__ tinfo, int64_t T, float c, int seg,
+                     int *__restrict__ kept, int *__restrict__ kcount, int *__restrict__ items) {
     __shared__ int sq[64];
     __shared__ float sthr[64];
     __shared__ int wcnt[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cnt = *fix_count, G = *n_groups;
+    const int cnt = *fix_count, G = (cnt + 63) / 64;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *n_groups = G;
     const float sqc = sqrtf(c);
     for (int g = blockIdx.x; g < G; g += gridDim.x) {
         const int rows = min(64, cnt - g * 64);
         __syncthreads();
         if (threadIdx.x < rows) {
-            sq[threadIdx.x] = order[g * 64 + threadIdx.x];
-            sthr[threadIdx.x] = thr_s[g * 64 + threadIdx.x];
+            const int q = (int)order[g * 64 + threadIdx.x];
+            sq[threadIdx.x] = q;
+            sthr[threadIdx.x] = thr[q];
         }
         __syncthreads();
         int base = 0;
@@ -1126,36 +1140,9 @@ tc_group_keep_kernel(const int *__restrict__ order, const float *__restrict__ th
     }
 }
 
-// Exclusive prefix sum of the groups' segment counts (one block; item_off has G + 1
-// entries).
-__global__ void __launch_bounds__(1024)
-tc_group_scan_kernel(const int *__restrict__ items, const int *__restrict__ n_groups, int *__restrict__ item_off) {
-    __shared__ int sdata[1024];
-    __shared__ int carry;
-    const int G = *n_groups;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < G; base += 1024) {
-        const int i = base + threadIdx.x;
-        sdata[threadIdx.x] = i < G ? items[i] : 0;
-        __syncthreads();
-        for (int o = 1; o < 1024; o <<= 1) {
-            const int v = threadIdx.x >= o ? sdata[threadIdx.x - o] : 0;
-            __syncthreads();
-            sdata[threadIdx.x] += v;
-            __syncthreads();
-        }
-        if (i < G) item_off[i + 1] = carry + sdata[threadIdx.x];
-        __syncthreads();
-        if (threadIdx.x == 1023) carry += sdata[1023];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) item_off[0] = 0;
-}
-
 // Per flagged query (sorted position j): the FP64 sum of its group's segment partials.
 __global__ void tc_group_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
-                                        const int *__restrict__ item_off, const int *__restrict__ order,
+                                        const int *__restrict__ item_off, const uint32_t *__restrict__ order,
                                         const int *__restrict__ fix_count, double scale, double *__restrict__ out) {
     const int cnt = *fix_count;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x) {
@@ -1171,18 +1158,21 @@ __global__ void tc_group_combine_kernel(const double *__restrict__ part_sum, con
 
 // FP64 combine of the per-split partials (as kde_combine.cu) plus the per-query error
 // estimate of the tensor-core form,
-//     est = a * (sum_t S_t w_t) / (sum_t S_t),   w_t = 2^-21 ||q - c_g|| r_t + beta rho_t^2,
-// S_t the query's sum over tile t, r_t that tile's RMS radius (the split products' error
-// grows with ||q - c_g|| |x - c_t|), rho_t its largest radius and beta = 2^-23 sqrt(MMA
-// steps) (the FP32 accumulation's error grows with ||x - c_t||^2; see tc_tile_radius).
-// The epilogue accumulates sum_t S_t w_t. Queries with est > thr (or an empty sum) are
-// appended to fix_idx for the plain FP32 form.
-__global__ void tc_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
-                                  const double *__restrict__ part_w, int64_t m, int splits, double scale,
-                                  const int *__restrict__ qbad, double a,
-                                  double thr, double *__restrict__ out, int *__restrict__ fix_idx,
-                                  int *__restrict__ fix_count, int *__restrict__ qflag) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+//     est = a * (sum_t S_t w_t) / (sum_t S_t),   w_t = max(2^-21 ||q - c_g|| r_t, beta rho_t^2),
+// S_t the query's sum over tile t, r_t that tile's RMS radius, rho_t its largest radius
+// and beta = 2^-23 sqrt(MMA steps). The first term (the split products' error grows with
+// ||q - c_g|| |x - c_t|) was calibrated on the whole arithmetic over spatially coherent
+// tiles, so it covers their FP32 accumulation error too; the second takes over where the
+// accumulation error of a tile's outlying points (it grows with ||x - c_t||^2; see
+// tc_tile_radius) exceeds it. The epilogue accumulates sum_t S_t w_t. Queries with
+// est > thr (or an empty sum) are appended to fix_idx for the plain FP32 form.
+__global__ void __launch_bounds__(256)
+tc_combine_kernel(const double *__restrict__ part_sum, const float *__restrict__ part_shift,
+                  const double *__restrict__ part_w, int64_t m, int splits, double scale, const int *__restrict__ qbad,
+                  double a, double thr, double *__restrict__ out, int *__restrict__ qflag, int *__restrict__ bcnt) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // one query per thread
+    bool flag = false;
+    if (j < m) {
         float smax = -INFINITY;
         for (int k = 0; k < splits; ++k) smax = fmaxf(smax, part_shift[(int64_t)k * m + j]);
         double tot = 0.0, wt = 0.0;
@@ -1195,10 +1185,11 @@ __global__ void tc_combine_kernel(const double *__restrict__ part_sum, const flo
         // tot is in units of 2^smax, a bound on every term: below 2^-40 the bound was too
         // loose for the fixed shift (terms under 2^-126 of it were flushed)
         const double est = (tot >= 0x1p-40 && !qbad[j]) ? a * (wt / tot) : INFINITY;
-        const bool flag = est > thr && fix_idx;
-        if (flag) fix_idx[atomicAdd(fix_count, 1)] = (int)j;
+        flag = est > thr && qflag;
         if (qflag) qflag[j] = flag ? 1 : 0;
     }
+    const int c = __syncthreads_count(flag);
+    if (bcnt && threadIdx.x == 0) bcnt[blockIdx.x] = c;
 }
 
 // ------------------------------------------------------------------ host helpers
@@ -1327,7 +1318,6 @@ void tc_free(stag_kde *h) {
     cudaFree(tc->ub);
     cudaFree(tc->part_w);
     cudaFree(tc->fix_idx);
-    cudaFree(tc->qflag);
     cudaFree(tc->gbuf);
     cudaFree(tc->fix_count);
     cudaFree(tc->err);
@@ -1428,8 +1418,8 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
 struct GroupScratch {
     uint64_t *key, *ktmp;
     uint32_t *val, *vtmp, *hist;
-    float *thr, *thr_s;
-    int *order, *kept, *kcount, *items, *item_off, *n_groups;
+    float *thr;
+    int *qflag, *bcnt, *boff, *kept, *kcount, *items, *item_off, *n_groups;
     double *psum;
     float *pshift;
 };
@@ -1440,6 +1430,7 @@ static int group_seg(int64_t T, int BN) { return (int)std::max<int64_t>(8 * 64 /
 
 static int64_t group_scratch_bytes(int64_t m, int64_t T, int BN, GroupScratch *gs, void *base) {
     const int64_t G = ceil_div(std::max<int64_t>(m, 1), 64);
+    const int64_t B = ceil_div(std::max<int64_t>(m, 1), 256);  // blocks of the combine kernel
     const int64_t items = G * ceil_div(T, group_seg(T, BN));  // at most 64 segments per group
     int64_t off = 0;
     auto take = [&](int64_t bytes) {
@@ -1455,8 +1446,9 @@ static int64_t group_scratch_bytes(int64_t m, int64_t T, int BN, GroupScratch *g
     g.vtmp = (uint32_t *)take(mm * 4);
     g.hist = (uint32_t *)take(radix_sort_hist_entries(mm) * 4);
     g.thr = (float *)take(mm * 4);
-    g.thr_s = (float *)take(mm * 4);
-    g.order = (int *)take(mm * 4);
+    g.qflag = (int *)take(mm * 4);
+    g.bcnt = (int *)take(B * 4);
+    g.boff = (int *)take((B + 1) * 4);
     g.kept = (int *)take(G * T * 4);
     g.kcount = (int *)take(G * 4);
     g.items = (int *)take(G * 4);
@@ -1489,8 +1481,6 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         cudaFree(tc->qbad);
         cudaFree(tc->ub);
         cudaFree(tc->fix_idx);
-        cudaFree(tc->qflag);
-        tc->qflag = nullptr;
         tc->unorm = nullptr;
         tc->qbad = nullptr;
         tc->ub = nullptr;
@@ -1500,7 +1490,6 @@ static int ensure_query_scratch(stag_kde *h, int64_t m_pad) {
         STAG_CUDA_TRY(dev_malloc(&tc->qbad, m_pad * sizeof(int)));
         STAG_CUDA_TRY(dev_malloc(&tc->ub, m_pad * sizeof(unsigned)));
         STAG_CUDA_TRY(dev_malloc(&tc->fix_idx, m_pad * sizeof(int)));
-        STAG_CUDA_TRY(dev_malloc(&tc->qflag, m_pad * sizeof(int)));
         tc->unorm_cap = m_pad;
     }
     if (!tc->fix_count) STAG_CUDA_TRY(dev_malloc(&tc->fix_count, sizeof(int)));
@@ -1624,39 +1613,43 @@ static void fill_inst(const stag_kde *h, int64_t m, int64_t q_tiles, int64_t spl
     I->units = q_tiles * splits;
 }
 
-// Grouped recompute of the flagged queries, all on stream s.
+// Grouped recompute of the flagged queries, all on stream s (after tc_combine_kernel has
+// written the per-query flags and per-block counts into the scratch).
 static int tc_fixup_grouped(stag_kde *h, const float *dQ, int64_t m, double *dOut, cudaStream_t s) {
     TcData *tc = h->tc;
     GroupScratch g;
     group_scratch_bytes(m, tc->T, tc->BN, &g, tc->gbuf);
     const int64_t m_pad = round_up(m, BM);
+    const int64_t B = ceil_div(m, 256);
     const float c = (float)(h->a * 1.4426950408889634);
     const int seg = group_seg(tc->T, tc->BN);
     const int per = tc->BN / kSimtTile;
-    count_launch(3);
-    tc_group_key_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 8), (int64_t)h->sm_count * 16), 256, 0, s>>>(
-        tc->qflag, m, m_pad, tc->rowterm, tc->tinfo, tc->T, c, g.key, g.val, g.thr);
+    count_launch(2);
+    // the flagged queries in query order (their count into fix_count), with sort keys
+    tc_scan_kernel<<<1, 1024, 0, s>>>(g.bcnt, nullptr, (int)B, g.boff, tc->fix_count);
+    tc_flag_compact_kernel<<<(unsigned)B, 256, 0, s>>>(g.qflag, g.boff, m, m_pad, tc->rowterm, tc->tinfo, tc->T, c,
+                                                       tc->fix_idx, g.key, g.val, g.thr);
     STAG_CUDA_TRY(cudaGetLastError());
-    int bits = 1;  // tile indices and the sentinel T
-    while (((int64_t)1 << bits) <= tc->T) ++bits;
-    int rc = radix_sort_pairs(g.key, g.val, g.ktmp, g.vtmp, g.hist, m, bits, s);
+    // stable sort by leading tile of the flagged entries only (device count): the input
+    // is in query order, so the groups are deterministic
+    int bits = 1;
+    while (((int64_t)1 << bits) < tc->T) ++bits;
+    int rc = radix_sort_pairs(g.key, g.val, g.ktmp, g.vtmp, g.hist, m, bits, s, tc->fix_count);
     if (rc) return rc;
-    tc_group_order_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1024), 256, 0, s>>>(
-        g.val, tc->fix_count, g.thr, g.order, g.thr_s, g.n_groups);
-    rc = simt_gather_rows(h, dQ, g.order, tc->fix_count, m, h->qt, s);
+    rc = simt_gather_rows(h, dQ, reinterpret_cast<const int *>(g.val), tc->fix_count, m, h->qt, s);
     if (rc) return rc;
-    tc_group_keep_kernel<<<(unsigned)(h->sm_count * 4), 256, 0, s>>>(g.order, g.thr_s, tc->fix_count, g.n_groups,
-                                                                      m_pad, tc->rowterm, tc->tinfo, tc->T, c, seg,
-                                                                      g.kept, g.kcount, g.items);
-    count_launch();
-    tc_group_scan_kernel<<<1, 1024, 0, s>>>(g.items, g.n_groups, g.item_off);
+    count_launch(2);
+    tc_group_keep_kernel<<<(unsigned)(h->sm_count * 4), 256, 0, s>>>(g.val, g.thr, tc->fix_count, g.n_groups, m_pad,
+                                                                      tc->rowterm, tc->tinfo, tc->T, c, seg, g.kept,
+                                                                      g.kcount, g.items);
+    tc_scan_kernel<<<1, 1024, 0, s>>>(g.items, tc->fix_count, 0, g.item_off, nullptr);
     STAG_CUDA_TRY(cudaGetLastError());
     rc = simt_list_launch(h, tc->xkt, h->qt, g.kept, tc->T, g.kcount, g.item_off, g.n_groups, seg, per, g.psum,
                           g.pshift, s);
     if (rc) return rc;
     count_launch();
     tc_group_combine_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 1024), 256, 0, s>>>(
-        g.psum, g.pshift, g.item_off, g.order, tc->fix_count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
+        g.psum, g.pshift, g.item_off, g.val, tc->fix_count, h->normalise ? 1.0 / (double)h->n : 1.0, dOut);
     STAG_CUDA_TRY(cudaGetLastError());
     return 0;
 }
@@ -1666,12 +1659,12 @@ static int tc_fixup_grouped(stag_kde *h, const float *dQ, int64_t m, double *dOu
 static int tc_finish(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {
     TcData *tc = h->tc;
     const bool check = h->tc_check;
-    if (check) STAG_CUDA_TRY(cudaMemsetAsync(tc->fix_count, 0, sizeof(int), s));
+    GroupScratch g{};
+    if (check) group_scratch_bytes(m, tc->T, tc->BN, &g, tc->gbuf);
     count_launch();
-    tc_combine_kernel<<<(unsigned)std::min<int64_t>(ceil_div(m, 256), 4096), 256, 0, s>>>(
-        h->part.sum, h->part.shift, tc->part_w, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0,
-        tc->qbad, h->a, kTcErrThreshold, dOut, check ? tc->fix_idx : nullptr, tc->fix_count,
-        check ? tc->qflag : nullptr);
+    tc_combine_kernel<<<(unsigned)ceil_div(m, 256), 256, 0, s>>>(
+        h->part.sum, h->part.shift, tc->part_w, m, (int)splits, h->normalise ? 1.0 / (double)h->n : 1.0, tc->qbad,
+        h->a, kTcErrThreshold, dOut, check ? g.qflag : nullptr, check ? g.bcnt : nullptr);
     STAG_CUDA_TRY(cudaGetLastError());
     if (!check) return 0;
     // groups of 64 flagged queries share every point load (a per-query pass would re-read
