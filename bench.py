@@ -491,6 +491,13 @@ def measure(args, workload, lib, dev, world, rank, local, steps, warmup, with_cp
         for _ in range(warmup):
             step()
     torch.cuda.synchronize()
+    if args.profile_one_step:
+        # one untimed step bracketed for a profiler started with --profile-from-start off
+        torch.cuda.profiler.start()
+        with torch.cuda.stream(stream):
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
 
     # timed region: K steps, each bracketed by events on the launching stream; L2 flushed
     # between steps outside the brackets
@@ -890,6 +897,12 @@ def run_batched(args):
     for _ in range(args.warmup):
         query_batch(kdes, Qs, outs, stream)
     torch.cuda.synchronize()
+    if args.profile_one_step:
+        # one untimed replay bracketed for a profiler started with --profile-from-start off
+        torch.cuda.profiler.start()
+        query_batch(kdes, Qs, outs, stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(0)
@@ -967,7 +980,7 @@ def run_serving(args):
 
         def run(rate, duration, closed=False):
             lib.stag_srv_reset_stats(srv)
-            tickets = []
+            tickets = []   # (ticket, out): each output buffer stays alive until its wait returns
             kept = []  # (dataset, Q, out) of the sampled requests
             lock = threading.Lock()
             stop = threading.Event()
@@ -979,7 +992,7 @@ def run_serving(args):
                     if t is None:
                         time.sleep(0.0005)
                         continue
-                    lib.stag_srv_wait(srv, t, -1)
+                    lib.stag_srv_wait(srv, t[0], -1)
 
             th = threading.Thread(target=waiter)
             th.start()
@@ -1007,7 +1020,7 @@ def run_serving(args):
                 L.check(lib.stag_srv_submit(srv, j, Q.ctypes.data, Q.shape[0], out.ctypes.data, ctypes.byref(t)))
                 pairs += Q.shape[0] * ns[j]
                 with lock:
-                    tickets.append(t.value)
+                    tickets.append((t.value, out))
             stop.set()
             th.join()
             el = time.perf_counter() - t0
@@ -1123,6 +1136,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the large (n=2e6, d=64) object of the default line")
     ap.add_argument("--acc-queries", type=int, default=None, help="cap on the oracle sample used for the accuracy")
+    ap.add_argument("--profile-one-step", action="store_true",
+                    help="bracket one untimed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--count", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--serve-duration", type=float, default=60.0, help="seconds per offered load (serving)")
     ap.add_argument("--serve-pool", type=int, default=4096, help="pre-generated requests (serving)")

@@ -897,99 +897,145 @@ __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, in
 // hi/lo pairs (the MMA's A operand; the difference and scale in FP64, u_lo = u - u_hi)
 // and flags, in qbad, a query farther from the data than that range (its row is zeroed and
 // the combine hands it to the plain FP32 form).
-// One thread per query (its coordinates in registers), 128 queries per block, the tile
-// centres of a group of 32 tiles staged in shared memory and read as broadcasts.
+// 128 queries per block. A thread holds two queries (2p, 2p+1) over a slice of CPT <= 32
+// coordinates as packed pairs (q_2p,k, q_2p+1,k), so one FP32x2 subtraction and one FMA
+// serve both queries and every tile centre read from shared memory (broadcast, 16 bytes
+// at a time) serves two queries: the centre loads, which bound a one-query-per-thread
+// form, are cut by 2 x KP / CPT. The LPP = KP / CPT lanes of a query pair are adjacent and
+// add their slices with shuffles. Tile centres are staged 32 tiles at a time.
 template <int KP>
-__global__ void __launch_bounds__(128)
+struct RowTermGeo {
+    static constexpr int CPT = KP < 32 ? KP : 32;  // coordinates per thread
+    static constexpr int LPP = KP / CPT;            // lanes per query pair
+    static constexpr int THREADS = 64 * LPP;        // 128 queries per block
+};
+
+template <int KP>
+__global__ void __launch_bounds__(RowTermGeo<KP>::THREADS)
 tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_pad, const float *__restrict__ cent,
                   int64_t T, int tiles_per_block, float c, float *__restrict__ R, const float *__restrict__ cg,
                   float *__restrict__ unorm, const float *__restrict__ tinfo, unsigned *__restrict__ ub,
                   const float *__restrict__ scales, __half *__restrict__ ahi, __half *__restrict__ alo,
                   int *__restrict__ qbad) {
-    constexpr int TG = 32;  // tiles per shared-memory group
+    using RG = RowTermGeo<KP>;
+    constexpr int CPT = RG::CPT, LPP = RG::LPP, TG = 32;  // TG: tiles per shared-memory group
     __shared__ __align__(16) float sc[TG][KP];
     __shared__ float srad[TG];
     const int64_t q0 = (int64_t)blockIdx.x * 128;
-    const int r = threadIdx.x;
-    const bool real = q0 + r < m;
+    const int pair = threadIdx.x / LPP, part = threadIdx.x % LPP;
+    const int k0 = part * CPT;                      // first coordinate of this lane's slice
+    const int64_t qa = q0 + 2 * pair, qb = qa + 1;  // the two queries
+    const bool ra = qa < m, rb = qb < m;
     if (blockIdx.y == 0) {
         // ||q - c_g|| and the A operand: FP16 hi/lo splits of u, zero for padding rows and
         // coordinates, stored eight coordinates (16 bytes) at a time
         const double su = scales[1];
-        float s = 0.f;
-        bool bad = false;
-        uint4 *dh = reinterpret_cast<uint4 *>(ahi + (q0 + r) * KP);
-        uint4 *dl = reinterpret_cast<uint4 *>(alo + (q0 + r) * KP);
+        float s2[2] = {0.f, 0.f};
+        int bad[2] = {0, 0};
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+            const int64_t q = w ? qb : qa;
+            const bool real = w ? rb : ra;
+            uint4 *dh = reinterpret_cast<uint4 *>(ahi + q * KP + k0);
+            uint4 *dl = reinterpret_cast<uint4 *>(alo + q * KP + k0);
 #pragma unroll 1
-        for (int k8 = 0; k8 < KP / 8; ++k8) {
-            __align__(16) __half hv[8], lv[8];
+            for (int k8 = 0; k8 < CPT / 8; ++k8) {
+                __align__(16) __half hv[8], lv[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int k = k8 * 8 + j;
-                __half hh = __float2half_rn(0.f), ll = __float2half_rn(0.f);
-                if (real && k < d) {
-                    const float qk = Q[(q0 + r) * d + k];
-                    const float df = qk - cg[k];
-                    s = fmaf(df, df, s);
-                    const double u = ((double)qk - (double)cg[k]) * su;
-                    if (fabs(u) < 0x1p15) {
-                        hh = __float2half_rn((float)u);
-                        ll = __float2half_rn((float)(u - (double)__half2float(hh)));
-                    } else {
-                        bad = true;
+                for (int j = 0; j < 8; ++j) {
+                    const int k = k0 + k8 * 8 + j;
+                    __half hh = __float2half_rn(0.f), ll = __float2half_rn(0.f);
+                    if (real && k < d) {
+                        const float qk = Q[q * d + k];
+                        const float df = qk - cg[k];
+                        s2[w] = fmaf(df, df, s2[w]);
+                        const double u = ((double)qk - (double)cg[k]) * su;
+                        if (fabs(u) < 0x1p15) {
+                            hh = __float2half_rn((float)u);
+                            ll = __float2half_rn((float)(u - (double)__half2float(hh)));
+                        } else {
+                            bad[w] = 1;
+                        }
                     }
+                    hv[j] = hh;
+                    lv[j] = ll;
                 }
-                hv[j] = hh;
-                lv[j] = ll;
+                dh[k8] = *reinterpret_cast<const uint4 *>(hv);
+                dl[k8] = *reinterpret_cast<const uint4 *>(lv);
             }
-            dh[k8] = *reinterpret_cast<const uint4 *>(hv);
-            dl[k8] = *reinterpret_cast<const uint4 *>(lv);
         }
-        unorm[q0 + r] = real ? sqrtf(s) : 0.f;
-        if (bad) qbad[q0 + r] = 1;
+        // the pair's lanes add their slices (and combine their out-of-range flags)
+#pragma unroll
+        for (int o = 1; o < LPP; o <<= 1) {
+            s2[0] += __shfl_xor_sync(0xffffffffu, s2[0], o);
+            s2[1] += __shfl_xor_sync(0xffffffffu, s2[1], o);
+            bad[0] |= __shfl_xor_sync(0xffffffffu, bad[0], o);
+            bad[1] |= __shfl_xor_sync(0xffffffffu, bad[1], o);
+        }
+        if (part == 0) {
+            unorm[qa] = ra ? sqrtf(s2[0]) : 0.f;
+            unorm[qb] = rb ? sqrtf(s2[1]) : 0.f;
+            if (bad[0]) qbad[qa] = 1;
+            if (bad[1]) qbad[qb] = 1;
+        }
     }
-    float qv[KP];
+    // the queries' slices as packed pairs (query 2p in the low half, 2p + 1 in the high)
+    uint64_t qp[CPT];
 #pragma unroll
-    for (int k = 0; k < KP; ++k) qv[k] = (real && k < d) ? Q[(q0 + r) * d + k] : 0.f;
-    // the query as packed coordinate pairs: two differences and two FMAs per instruction
-    uint64_t qp[KP / 2];
-#pragma unroll
-    for (int k = 0; k < KP / 2; ++k) qp[k] = f2::pack(qv[2 * k], qv[2 * k + 1]);
+    for (int k = 0; k < CPT; ++k) {
+        const int kk = k0 + k;
+        qp[k] = f2::pack((ra && kk < d) ? Q[qa * d + kk] : 0.f, (rb && kk < d) ? Q[qb * d + kk] : 0.f);
+    }
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
     // upper bound on the exponent -c ||q - x||^2 over the tiles of this block: every x of
     // tile t lies within the tile's max radius rho_t of c_t, so
     //     -c ||q - x||^2 <= -( max(0, sqrt(c R') - sqrt(c) rho_t) )^2,  R' = ||q - c_t||^2
     const float sqc = sqrtf(c);
-    float ubest = -INFINITY;
+    float ubest_a = -INFINITY, ubest_b = -INFINITY;
     for (int64_t g0 = ta; g0 < tb; g0 += TG) {
         const int gn = (int)min((int64_t)TG, tb - g0);
         __syncthreads();
-        for (int e = threadIdx.x; e < gn * KP; e += 128) sc[e / KP][e % KP] = cent[(g0 + e / KP) * KP + e % KP];
-        for (int e = threadIdx.x; e < gn; e += 128) srad[e] = tinfo[(g0 + e) * 4 + 1];
+        for (int e = threadIdx.x; e < gn * KP; e += RG::THREADS) sc[e / KP][e % KP] = cent[(g0 + e / KP) * KP + e % KP];
+        for (int e = threadIdx.x; e < gn; e += RG::THREADS) srad[e] = tinfo[(g0 + e) * 4 + 1];
         __syncthreads();
         for (int j = 0; j < gn; ++j) {
-            uint64_t a01 = 0, a23 = 0;  // {0.f, 0.f}
+            uint64_t acc0 = 0, acc1 = 0;  // {0.f, 0.f}: two chains over the slice
 #pragma unroll
-            for (int k = 0; k < KP; k += 4) {
-                const float4 cv = *reinterpret_cast<const float4 *>(&sc[j][k]);
-                const uint64_t d01 = f2::sub(qp[k / 2], f2::pack(cv.x, cv.y));
-                const uint64_t d23 = f2::sub(qp[k / 2 + 1], f2::pack(cv.z, cv.w));
-                a01 = f2::fma(d01, d01, a01);
-                a23 = f2::fma(d23, d23, a23);
+            for (int k = 0; k < CPT; k += 4) {
+                const float4 cv = *reinterpret_cast<const float4 *>(&sc[j][k0 + k]);
+                const uint64_t d0 = f2::sub(qp[k], f2::pack(cv.x, cv.x));
+                const uint64_t d1 = f2::sub(qp[k + 1], f2::pack(cv.y, cv.y));
+                const uint64_t d2 = f2::sub(qp[k + 2], f2::pack(cv.z, cv.z));
+                const uint64_t d3 = f2::sub(qp[k + 3], f2::pack(cv.w, cv.w));
+                acc0 = f2::fma(d0, d0, acc0);
+                acc1 = f2::fma(d1, d1, acc1);
+                acc0 = f2::fma(d2, d2, acc0);
+                acc1 = f2::fma(d3, d3, acc1);
             }
-            float s0, s1, s2, s3;
-            f2::unpack(a01, s0, s1);
-            f2::unpack(a23, s2, s3);
-            const float cr = c * ((s0 + s1) + (s2 + s3));
-            R[(g0 + j) * m_pad + q0 + r] = real ? cr : 0.f;
+            float sa, sb;
+            f2::unpack(f2::add(acc0, acc1), sa, sb);
+#pragma unroll
+            for (int o = 1; o < LPP; o <<= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, o);
+                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            }
+            const float cra = c * sa, crb = c * sb;
+            if (part == 0)
+                *reinterpret_cast<float2 *>(&R[(g0 + j) * m_pad + qa]) = make_float2(ra ? cra : 0.f, rb ? crb : 0.f);
             // slack of 1e-5 relative (far above the approximate square root's ~2^-22 error
             // and the FP32 rounding of the exponents) so that the bound holds
-            const float gap = fmaxf(0.f, ptx::sqrt_approx(cr) * (1.f - 1e-5f) - sqc * srad[j]);
-            ubest = fmaxf(ubest, -gap * gap);
+            const float rr = sqc * srad[j];
+            const float ga = fmaxf(0.f, ptx::sqrt_approx(cra) * (1.f - 1e-5f) - rr);
+            const float gb = fmaxf(0.f, ptx::sqrt_approx(crb) * (1.f - 1e-5f) - rr);
+            ubest_a = fmaxf(ubest_a, -ga * ga);
+            ubest_b = fmaxf(ubest_b, -gb * gb);
         }
     }
-    if (tb > ta) atomicMax(ub + q0 + r, float_order_bits(real ? ubest : 0.f));
+    if (tb > ta && part == 0) {
+        atomicMax(ub + qa, float_order_bits(ra ? ubest_a : 0.f));
+        atomicMax(ub + qb, float_order_bits(rb ? ubest_b : 0.f));
+    }
 }
 
 // FP32 recompute of the queries the tensor-core estimate flags, over the tiles that can
@@ -1571,7 +1617,8 @@ static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     switch (Kp) {
 #define STAG_ROWTERM(KPV)                                                                                          \
     case KPV:                                                                                                      \
-        tc_rowterm_kernel<KPV><<<grid, 128, 0, s>>>(dQ, m, h->d, m_pad, tc->cent, tc->T, tpb, (float)c, tc->rowterm, \
+        tc_rowterm_kernel<KPV><<<grid, RowTermGeo<KPV>::THREADS, 0, s>>>(dQ, m, h->d, m_pad, tc->cent, tc->T, tpb,   \
+                                                                         (float)c, tc->rowterm,                   \
                                                     tc->cg, tc->unorm, tc->tinfo, tc->ub, tc->scales, tc->a_hi,    \
                                                     tc->a_lo, tc->qbad);                                           \
         break;
