@@ -899,10 +899,11 @@ __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, in
 // the combine hands it to the plain FP32 form).
 // 128 queries per block. A thread holds two queries (2p, 2p+1) over a slice of CPT <= 32
 // coordinates as packed pairs (q_2p,k, q_2p+1,k), so one FP32x2 subtraction and one FMA
-// serve both queries and every tile centre read from shared memory (broadcast, 16 bytes
-// at a time) serves two queries: the centre loads, which bound a one-query-per-thread
-// form, are cut by 2 x KP / CPT. The LPP = KP / CPT lanes of a query pair are adjacent and
-// add their slices with shuffles. Tile centres are staged 32 tiles at a time.
+// serve both queries, and every centre coordinate read from shared memory (stored twice,
+// (c_k, c_k), 16 bytes = two coordinates per broadcast load) serves two queries: half the
+// shared-memory loads of a one-query-per-thread form. The LPP = KP / CPT lanes of a query
+// pair are adjacent and add their slices with shuffles. Tile centres are staged 32 tiles
+// at a time.
 template <int KP>
 struct RowTermGeo {
     static constexpr int CPT = KP < 32 ? KP : 32;  // coordinates per thread
@@ -919,7 +920,13 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
                   int *__restrict__ qbad) {
     using RG = RowTermGeo<KP>;
     constexpr int CPT = RG::CPT, LPP = RG::LPP, TG = 32;  // TG: tiles per shared-memory group
-    __shared__ __align__(16) float sc[TG][KP];
+    // every centre coordinate twice: one 16-byte load gives two packed operands (c_k, c_k),
+    // (c_k+1, c_k+1) for the query pair. The same bytes first stage the block's queries,
+    // 64 at a time, rows padded by one float against bank conflicts.
+    constexpr int SC_BYTES = TG * KP * 8, SQ_BYTES = 64 * (KP + 1) * 4;
+    __shared__ __align__(16) unsigned char smem_raw[SC_BYTES > SQ_BYTES ? SC_BYTES : SQ_BYTES];
+    auto sc = reinterpret_cast<uint64_t (*)[KP]>(smem_raw);
+    float *sq = reinterpret_cast<float *>(smem_raw);
     __shared__ float srad[TG];
     const int64_t q0 = (int64_t)blockIdx.x * 128;
     const int pair = threadIdx.x / LPP, part = threadIdx.x % LPP;
@@ -979,12 +986,24 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
             if (bad[1]) qbad[qb] = 1;
         }
     }
-    // the queries' slices as packed pairs (query 2p in the low half, 2p + 1 in the high)
+    // the queries' slices as packed pairs (query 2p in the low half, 2p + 1 in the high),
+    // read from shared memory after a coalesced copy of 64 query rows at a time
     uint64_t qp[CPT];
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const int64_t r0 = q0 + 64 * h;
+        for (int e = threadIdx.x; e < 64 * KP; e += RG::THREADS) {
+            const int r = e / KP, k = e % KP;
+            sq[r * (KP + 1) + k] = (r0 + r < m && k < d) ? Q[(r0 + r) * d + k] : 0.f;
+        }
+        __syncthreads();
+        if ((2 * pair) / 64 == h) {
+            const int la = 2 * pair - 64 * h;
 #pragma unroll
-    for (int k = 0; k < CPT; ++k) {
-        const int kk = k0 + k;
-        qp[k] = f2::pack((ra && kk < d) ? Q[qa * d + kk] : 0.f, (rb && kk < d) ? Q[qb * d + kk] : 0.f);
+            for (int k = 0; k < CPT; ++k)
+                qp[k] = f2::pack(sq[la * (KP + 1) + k0 + k], sq[(la + 1) * (KP + 1) + k0 + k]);
+        }
+        __syncthreads();
     }
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
@@ -995,26 +1014,30 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
     float ubest_a = -INFINITY, ubest_b = -INFINITY;
     for (int64_t g0 = ta; g0 < tb; g0 += TG) {
         const int gn = (int)min((int64_t)TG, tb - g0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < gn * KP; e += RG::THREADS) sc[e / KP][e % KP] = cent[(g0 + e / KP) * KP + e % KP];
+        if (g0 > ta) __syncthreads();
+        for (int e = threadIdx.x; e < gn * KP; e += RG::THREADS) {
+            const float cv = cent[(g0 + e / KP) * KP + e % KP];
+            sc[e / KP][e % KP] = f2::pack(cv, cv);
+        }
         for (int e = threadIdx.x; e < gn; e += RG::THREADS) srad[e] = tinfo[(g0 + e) * 4 + 1];
         __syncthreads();
         for (int j = 0; j < gn; ++j) {
-            uint64_t acc0 = 0, acc1 = 0;  // {0.f, 0.f}: two chains over the slice
+            uint64_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;  // {0.f, 0.f}: four chains
 #pragma unroll
             for (int k = 0; k < CPT; k += 4) {
-                const float4 cv = *reinterpret_cast<const float4 *>(&sc[j][k0 + k]);
-                const uint64_t d0 = f2::sub(qp[k], f2::pack(cv.x, cv.x));
-                const uint64_t d1 = f2::sub(qp[k + 1], f2::pack(cv.y, cv.y));
-                const uint64_t d2 = f2::sub(qp[k + 2], f2::pack(cv.z, cv.z));
-                const uint64_t d3 = f2::sub(qp[k + 3], f2::pack(cv.w, cv.w));
+                const ulonglong2 c01 = *reinterpret_cast<const ulonglong2 *>(&sc[j][k0 + k]);
+                const ulonglong2 c23 = *reinterpret_cast<const ulonglong2 *>(&sc[j][k0 + k + 2]);
+                const uint64_t d0 = f2::sub(qp[k], c01.x);
+                const uint64_t d1 = f2::sub(qp[k + 1], c01.y);
+                const uint64_t d2 = f2::sub(qp[k + 2], c23.x);
+                const uint64_t d3 = f2::sub(qp[k + 3], c23.y);
                 acc0 = f2::fma(d0, d0, acc0);
                 acc1 = f2::fma(d1, d1, acc1);
-                acc0 = f2::fma(d2, d2, acc0);
-                acc1 = f2::fma(d3, d3, acc1);
+                acc2 = f2::fma(d2, d2, acc2);
+                acc3 = f2::fma(d3, d3, acc3);
             }
             float sa, sb;
-            f2::unpack(f2::add(acc0, acc1), sa, sb);
+            f2::unpack(f2::add(f2::add(acc0, acc1), f2::add(acc2, acc3)), sa, sb);
 #pragma unroll
             for (int o = 1; o < LPP; o <<= 1) {
                 sa += __shfl_xor_sync(0xffffffffu, sa, o);
@@ -1121,12 +1144,24 @@ tc_flag_compact_kernel(const int *__restrict__ qflag, const int *__restrict__ bo
     float best = -INFINITY;
     int bt = 0;
     if (flag) {
-        for (int t = 0; t < (int)T; ++t) {
-            const float h2 = sqrtf(R[(int64_t)t * m_pad + j]) * (1.f + 1e-5f) + sqc * tinfo[(int64_t)t * 4 + 1];
-            const float lb = -h2 * h2;
-            if (lb > best) {  // ties keep the smaller tile
-                best = lb;
-                bt = t;
+        // eight row terms in flight per thread (the loads of a warp's 32 queries coalesce)
+        constexpr int U = 8;
+        for (int t0 = 0; t0 < (int)T; t0 += U) {
+            float rv[U], rho[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = min(t0 + u, (int)T - 1);
+                rv[u] = R[(int64_t)t * m_pad + j];
+                rho[u] = tinfo[(int64_t)t * 4 + 1];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const float h2 = sqrtf(rv[u]) * (1.f + 1e-5f) + sqc * rho[u];
+                const float lb = -h2 * h2;
+                if (t0 + u < (int)T && lb > best) {  // ties keep the smaller tile
+                    best = lb;
+                    bt = t0 + u;
+                }
             }
         }
         fix_idx[w] = (int)j;
@@ -1610,8 +1645,8 @@ static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     STAG_CUDA_TRY(cudaMemsetAsync(tc->qbad, 0, m_pad * sizeof(int), s));
     STAG_CUDA_TRY(cudaMemsetAsync(tc->ub, 0, m_pad * sizeof(unsigned), s));
     count_launch(1);
-    // tiles per block: 64, fewer when that leaves under ~4 blocks per SM (small batches)
-    int tpb = 64;
+    // tiles per block: 256, fewer when that leaves under ~4 blocks per SM (small batches)
+    int tpb = 256;
     while (tpb > 8 && (m_pad / BM) * ceil_div(tc->T, tpb) < 4 * (int64_t)h->sm_count) tpb /= 2;
     dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
     switch (Kp) {
