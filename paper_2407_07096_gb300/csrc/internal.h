@@ -194,8 +194,11 @@ size_t tc_inst_size();
 int tc_prep_public(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s);
 int64_t tc_fill_inst(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t unit_begin, void *inst,
                      int64_t *splits);
-int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total_units, int *err, int sm_count,
-                    uint64_t wait_ns, cudaStream_t s);
+// One persistent launch for every operand width (16, 32, 64, 128 at index 0..3): table c
+// holds n_inst[c] instances with units[c] units in all; work[c] (any unit, 0 for an empty
+// width) sizes the width's share of the CTAs.
+int tc_launch_multi(int eg, const void *const tables[4], const int n_inst[4], const int64_t units[4],
+                    const double work[4], int *err, int sm_count, uint64_t wait_ns, cudaStream_t s);
 int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s);
 // kde_batch.cu
 void batch_forget_handle(stag_kde *h);

@@ -3,9 +3,10 @@
 // Many independent instances (each a handle with its own point set, d and a, and a query
 // batch of its own size) are evaluated together:
 //   * query-side preparation of every instance;
-//   * ONE persistent tensor-core launch per operand width (16/32/64/128) whose work list
-//     spans the units (query tile, range of point tiles) of every instance of that width,
-//     read from a device table of instances (kde_tc.cu, TcInst);
+//   * ONE persistent tensor-core launch for every operand width (16/32/64/128): its CTAs
+//     are split into one range per width, sized by the width's share of the work, and each
+//     range walks the units (query tile, range of point tiles) of every instance of its
+//     width, read from a device table of instances (kde_tc.cu, TcInst, TcMulti);
 //   * per instance: FP64 combine with the error estimate and the FP32 recompute of flagged
 //     queries; instances on the plain forms run their usual path.
 // The whole sequence is captured once into a CUDA graph and replayed on later calls with
@@ -31,8 +32,13 @@ struct ClassLaunch {
     int Kp = 0;
     int n_inst = 0;
     int64_t total_units = 0;
+    double work = 0.0;        // SM time of the width's pairs, in units of one ex2 per pair
     void *d_table = nullptr;  // device copy of the instance table
 };
+
+// Relative SM time of one pair at operand width Kp: the slower of one ex2 (32 per SM per
+// clock) and the form's 2 (3 Kp + 16) MMA flops (8192 per SM per clock).
+double pair_cost(int Kp) { return std::max(1.0, (3.0 * Kp + 16.0) / 128.0); }
 
 struct BatchPlan {
     std::vector<uintptr_t> key;
@@ -126,6 +132,7 @@ int build_tables(BatchPlan *p) {
             const int64_t units = tc_fill_inst(h, p->ms[i], p->tiles_per_unit, cl.total_units,
                                                host.data() + host.size() - isz, &p->splits[i]);
             cl.total_units += units;
+            cl.work += (double)p->ms[i] * (double)h->n * pair_cost(Kp);
             ++cl.n_inst;
         }
         if (!cl.n_inst) continue;
@@ -163,10 +170,20 @@ int enqueue(BatchPlan *p, cudaStream_t s) {
         if (is_tc(h)) rc = tc_prep_public(h, (const float *)p->qs[i], p->ms[i], side_of(i));
     }
     if (!rc) rc = join();
-    for (auto &c : p->classes) {
-        if (rc) break;
-        rc = tc_launch_table(c.Kp, p->eg, c.d_table, c.n_inst, c.total_units, p->d_err, p->hs[0]->sm_count,
-                             p->wait_ns, s);
+    if (!rc && !p->classes.empty()) {
+        // one persistent launch for every width: each width's CTAs serve its table
+        const void *tables[4] = {nullptr, nullptr, nullptr, nullptr};
+        int n_inst[4] = {0, 0, 0, 0};
+        int64_t units[4] = {0, 0, 0, 0};
+        double work[4] = {0.0, 0.0, 0.0, 0.0};
+        for (auto &c : p->classes) {
+            const int w = c.Kp == 16 ? 0 : c.Kp == 32 ? 1 : c.Kp == 64 ? 2 : 3;
+            tables[w] = c.d_table;
+            n_inst[w] = c.n_inst;
+            units[w] = c.total_units;
+            work[w] = c.work;
+        }
+        rc = tc_launch_multi(p->eg, tables, n_inst, units, work, p->d_err, p->hs[0]->sm_count, p->wait_ns, s);
     }
     if (!rc) rc = fork();
     for (size_t i = 0; i < p->hs.size() && !rc; ++i) {

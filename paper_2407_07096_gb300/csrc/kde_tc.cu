@@ -76,6 +76,7 @@ struct TcData {
                                               //         the error estimate's accumulation weight
                                               //         FP32 distances), 0, 0
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
+    float *centT = nullptr;                   // [Kp][T]: the same, coordinate-major (row terms)
     float *cg = nullptr;                      // [Kp]: global centre c_g
     double *tsum = nullptr;                   // [T][Kp]: FP64 per-tile coordinate sums
     unsigned *vmax_bits = nullptr;            // max |x_k - c_t,k| (float bits)
@@ -282,11 +283,14 @@ __device__ __forceinline__ void epi_chunk(uint64_t &acc_a, uint64_t &acc_b, cons
     }
 }
 
+// The persistent tensor-core kernel's work, for one CTA of `ncta` serving the units of a
+// table of instances of one operand width: CTA number `cta` takes units cta, cta + ncta,
+// ... . `insts` points at kernel-parameter space when in_params (one instance; its tensor
+// maps are prefetched) or at a table in global memory.
 template <int KP, int BN, int SB, int SMETA, int AB, int EG>
-__global__ void __launch_bounds__(64 + 128 * EG, 1) __maxnreg__(EG >= 4 ? 112 : 200)
-kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ table, int n_inst,
-              int64_t total_units, int *err, uint64_t wait_ns, uint64_t stall_ns) {
-    const TcInst *insts = table ? table : &inst0;
+__device__ __forceinline__ void tc_body(const TcInst *__restrict__ insts, bool in_params, int n_inst,
+                                        int64_t total_units, int *err, uint64_t wait_ns, uint64_t stall_ns,
+                                        int cta, int ncta) {
     using C = Cfg<KP, BN, SB, SMETA, AB, EG>;
     using G = Geo<KP>;
     extern __shared__ uint8_t smem_raw[];
@@ -334,13 +338,13 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
         ptx::fence_proxy_async();
     }
     if (warp == 0 && lane == 0) {
-        if (!table) {
-            ptx::prefetch_tensormap(&inst0.map_ahi);
-            ptx::prefetch_tensormap(&inst0.map_alo);
-            ptx::prefetch_tensormap(&inst0.map_aaug);
-            ptx::prefetch_tensormap(&inst0.map_bhi);
-            ptx::prefetch_tensormap(&inst0.map_blo);
-            ptx::prefetch_tensormap(&inst0.map_baug);
+        if (in_params) {
+            ptx::prefetch_tensormap(&insts->map_ahi);
+            ptx::prefetch_tensormap(&insts->map_alo);
+            ptx::prefetch_tensormap(&insts->map_aaug);
+            ptx::prefetch_tensormap(&insts->map_bhi);
+            ptx::prefetch_tensormap(&insts->map_blo);
+            ptx::prefetch_tensormap(&insts->map_baug);
         }
     }
     if (warp == 1) {
@@ -369,7 +373,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
                 const uint64_t t0 = ptx::globaltimer();
                 while (ptx::globaltimer() - t0 < stall_ns && !*abort_flag) __nanosleep(1000);
             }
-            for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++ucount) {
+            for (int64_t u = cta; u < total_units && ok; u += ncta, ++ucount) {
                 if (*abort_flag) {  // another role gave up: issue nothing more
                     ok = false;
                     break;
@@ -447,7 +451,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             bool ok = true;
             const uint32_t a0 = ptx::smem_u32(smem + C::OFF_A);
             const uint32_t b0 = ptx::smem_u32(smem + C::OFF_B);
-            for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x, ++ucount) {
+            for (int64_t u = cta; u < total_units && ok; u += ncta, ++ucount) {
                 const TcInst &I = *find_inst(insts, n_inst, u);
                 const int64_t split = (u - I.unit_begin) / I.q_tiles;
                 const int64_t t0 = split * I.tiles_per_split;
@@ -639,7 +643,7 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
             st.w32 = fmaf(ts, vw, st.w32);
             return true;
         };
-        for (int64_t u = blockIdx.x; u < total_units && ok; u += gridDim.x) {
+        for (int64_t u = cta; u < total_units && ok; u += ncta) {
             // everything the tile loop needs is read once per unit, into registers
             const TcInst &I = *find_inst(insts, n_inst, u);
             const int64_t lu = u - I.unit_begin;
@@ -729,7 +733,53 @@ kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ t
     }
 }
 
+template <int KP, int BN, int SB, int SMETA, int AB, int EG>
+__global__ void __launch_bounds__(64 + 128 * EG, 1) __maxnreg__(EG >= 4 ? 112 : 200)
+kde_tc_kernel(const __grid_constant__ TcInst inst0, const TcInst *__restrict__ table, int n_inst,
+              int64_t total_units, int *err, uint64_t wait_ns, uint64_t stall_ns) {
+    tc_body<KP, BN, SB, SMETA, AB, EG>(table ? table : &inst0, table == nullptr, n_inst, total_units, err, wait_ns,
+                                       stall_ns, blockIdx.x, gridDim.x);
+}
+
+// Every operand width in one persistent launch (the batched path): the CTAs are split
+// into one contiguous range per width, sized by the width's share of the work; a range
+// serves its width's table of instances like a launch of its own.
+struct TcMulti {
+    const TcInst *table[4];  // widths 16, 32, 64, 128 (device tables; unused where n_inst = 0)
+    int n_inst[4];
+    int64_t units[4];
+    int cta_begin[5];        // CTA range of width c: [cta_begin[c], cta_begin[c + 1])
+};
+
+template <int EG>
+__global__ void __launch_bounds__(64 + 128 * EG, 1) __maxnreg__(EG >= 4 ? 112 : 200)
+kde_tc_multi_kernel(const __grid_constant__ TcMulti mp, int *err, uint64_t wait_ns, uint64_t stall_ns) {
+    const int b = blockIdx.x;
+    if (b < mp.cta_begin[1])
+        tc_body<16, 256, 4, 8, 2, EG>(mp.table[0], false, mp.n_inst[0], mp.units[0], err, wait_ns, stall_ns,
+                                      b - mp.cta_begin[0], mp.cta_begin[1] - mp.cta_begin[0]);
+    else if (b < mp.cta_begin[2])
+        tc_body<32, 256, 4, 8, 2, EG>(mp.table[1], false, mp.n_inst[1], mp.units[1], err, wait_ns, stall_ns,
+                                      b - mp.cta_begin[1], mp.cta_begin[2] - mp.cta_begin[1]);
+    else if (b < mp.cta_begin[3])
+        tc_body<64, 256, 2, 8, 1, EG>(mp.table[2], false, mp.n_inst[2], mp.units[2], err, wait_ns, stall_ns,
+                                      b - mp.cta_begin[2], mp.cta_begin[3] - mp.cta_begin[2]);
+    else if (b < mp.cta_begin[4])
+        tc_body<128, 128, 2, 8, 1, EG>(mp.table[3], false, mp.n_inst[3], mp.units[3], err, wait_ns, stall_ns,
+                                       b - mp.cta_begin[3], mp.cta_begin[4] - mp.cta_begin[3]);
+}
+
 // ------------------------------------------------------------------ prep kernels
+// The tile centres coordinate-major, centT[k][t] = cent[t][k] (the row-term kernel reads
+// 64 tiles' coordinate k with one coalesced load).
+__global__ void tc_transpose_centres_kernel(const float *__restrict__ cent, int64_t T, int Kp,
+                                            float *__restrict__ centT) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < T * Kp; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = i / T, t = i % T;
+        centT[i] = cent[t * Kp + k];
+    }
+}
+
 // Per-tile FP64 coordinate sums and FP32 centres (mean of the tile's real points).
 __global__ void tc_centres_kernel(const float *__restrict__ X, int64_t n, int64_t d, int BN, int Kp,
                                   double *__restrict__ tsum, float *__restrict__ cent) {
@@ -897,167 +947,183 @@ __global__ void tc_tile_radius_kernel(const float *__restrict__ X, int64_t n, in
 // hi/lo pairs (the MMA's A operand; the difference and scale in FP64, u_lo = u - u_hi)
 // and flags, in qbad, a query farther from the data than that range (its row is zeroed and
 // the combine hands it to the plain FP32 form).
-// 128 queries per block. A thread holds two queries (2p, 2p+1) over a slice of CPT <= 32
-// coordinates as packed pairs (q_2p,k, q_2p+1,k), so one FP32x2 subtraction and one FMA
-// serve both queries, and every centre coordinate read from shared memory (stored twice,
-// (c_k, c_k), 16 bytes = two coordinates per broadcast load) serves two queries: half the
-// shared-memory loads of a one-query-per-thread form. The LPP = KP / CPT lanes of a query
-// pair are adjacent and add their slices with shuffles. Tile centres are staged 32 tiles
-// at a time.
-template <int KP>
+// Register tiling: a block takes 128 queries and walks its range of point tiles 64 at a
+// time; a thread computes 8 queries (four packed pairs) x 4 tiles. The block's queries are
+// staged once, transposed ([k][query], dynamic shared memory); the centres of a chunk come
+// 16 coordinates at a time from their coordinate-major copy (coalesced), each stored twice
+// (c, c) so that one 64-bit operand serves a packed query pair. Per coordinate a thread
+// reads its queries' values and its four centres (four 16-byte loads) and spends 16 packed
+// subtractions and 16 packed FMAs: eight operations per shared-memory load. The sums run
+// in blocks of 16 coordinates (a fresh chain per block, added to the total), like the
+// plain form. Lane l of warp w: queries 32 (w % 4) + 8 (l % 4) .. +8, tiles 32 (w / 4) +
+// 4 (l / 4) .. +4 of the chunk, so a warp's query loads touch 128 bytes and its centre
+// loads 128 bytes (one wavefront each).
 struct RowTermGeo {
-    static constexpr int CPT = KP < 32 ? KP : 32;  // coordinates per thread
-    static constexpr int LPP = KP / CPT;            // lanes per query pair
-    static constexpr int THREADS = 64 * LPP;        // 128 queries per block
+    static constexpr int THREADS = 256;
+    static constexpr int TG = 64;       // tiles per chunk
+    static constexpr int KC = 16;       // coordinates per staged block of centres
+    static constexpr int QS = 128 + 4;  // row stride of the transposed queries (floats)
+    static constexpr int smem_bytes(int kp) { return kp * QS * 4; }
 };
 
 template <int KP>
-__global__ void __launch_bounds__(RowTermGeo<KP>::THREADS)
+__global__ void __launch_bounds__(RowTermGeo::THREADS, 2)
 tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_pad, const float *__restrict__ cent,
                   int64_t T, int tiles_per_block, float c, float *__restrict__ R, const float *__restrict__ cg,
                   float *__restrict__ unorm, const float *__restrict__ tinfo, unsigned *__restrict__ ub,
                   const float *__restrict__ scales, __half *__restrict__ ahi, __half *__restrict__ alo,
-                  int *__restrict__ qbad) {
-    using RG = RowTermGeo<KP>;
-    constexpr int CPT = RG::CPT, LPP = RG::LPP, TG = 32;  // TG: tiles per shared-memory group
-    // every centre coordinate twice: one 16-byte load gives two packed operands (c_k, c_k),
-    // (c_k+1, c_k+1) for the query pair. The same bytes first stage the block's queries,
-    // 64 at a time, rows padded by one float against bank conflicts.
-    constexpr int SC_BYTES = TG * KP * 8, SQ_BYTES = 64 * (KP + 1) * 4;
-    __shared__ __align__(16) unsigned char smem_raw[SC_BYTES > SQ_BYTES ? SC_BYTES : SQ_BYTES];
-    auto sc = reinterpret_cast<uint64_t (*)[KP]>(smem_raw);
-    float *sq = reinterpret_cast<float *>(smem_raw);
+                  int *__restrict__ qbad, const float *__restrict__ centT) {
+    using RG = RowTermGeo;
+    constexpr int TG = RG::TG, KC = RG::KC, QS = RG::QS;
+    extern __shared__ __align__(16) float sq[];              // [KP][QS]: the block's queries
+    __shared__ __align__(16) uint64_t sc[KC * TG];           // [k][tile slot]: (c, c)
     __shared__ float srad[TG];
     const int64_t q0 = (int64_t)blockIdx.x * 128;
-    const int pair = threadIdx.x / LPP, part = threadIdx.x % LPP;
-    const int k0 = part * CPT;                      // first coordinate of this lane's slice
-    const int64_t qa = q0 + 2 * pair, qb = qa + 1;  // the two queries
-    const bool ra = qa < m, rb = qb < m;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (blockIdx.y == 0) {
         // ||q - c_g|| and the A operand: FP16 hi/lo splits of u, zero for padding rows and
-        // coordinates, stored eight coordinates (16 bytes) at a time
+        // coordinates, stored eight coordinates (16 bytes) at a time; two threads per query
+        const int r = tid >> 1, part = tid & 1;
+        const int64_t q = q0 + r;
+        const bool real = q < m;
+        const int k0 = part * (KP / 2);
         const double su = scales[1];
-        float s2[2] = {0.f, 0.f};
-        int bad[2] = {0, 0};
-#pragma unroll
-        for (int w = 0; w < 2; ++w) {
-            const int64_t q = w ? qb : qa;
-            const bool real = w ? rb : ra;
-            uint4 *dh = reinterpret_cast<uint4 *>(ahi + q * KP + k0);
-            uint4 *dl = reinterpret_cast<uint4 *>(alo + q * KP + k0);
+        float s2 = 0.f;
+        int bad = 0;
+        uint4 *dh = reinterpret_cast<uint4 *>(ahi + q * KP + k0);
+        uint4 *dl = reinterpret_cast<uint4 *>(alo + q * KP + k0);
 #pragma unroll 1
-            for (int k8 = 0; k8 < CPT / 8; ++k8) {
-                __align__(16) __half hv[8], lv[8];
+        for (int k8 = 0; k8 < KP / 16; ++k8) {
+            __align__(16) __half hv[8], lv[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int k = k0 + k8 * 8 + j;
-                    __half hh = __float2half_rn(0.f), ll = __float2half_rn(0.f);
-                    if (real && k < d) {
-                        const float qk = Q[q * d + k];
-                        const float df = qk - cg[k];
-                        s2[w] = fmaf(df, df, s2[w]);
-                        const double u = ((double)qk - (double)cg[k]) * su;
-                        if (fabs(u) < 0x1p15) {
-                            hh = __float2half_rn((float)u);
-                            ll = __float2half_rn((float)(u - (double)__half2float(hh)));
-                        } else {
-                            bad[w] = 1;
-                        }
+            for (int j = 0; j < 8; ++j) {
+                const int k = k0 + k8 * 8 + j;
+                __half hh = __float2half_rn(0.f), ll = __float2half_rn(0.f);
+                if (real && k < d) {
+                    const float qk = Q[q * d + k];
+                    const float df = qk - cg[k];
+                    s2 = fmaf(df, df, s2);
+                    const double u = ((double)qk - (double)cg[k]) * su;
+                    if (fabs(u) < 0x1p15) {
+                        hh = __float2half_rn((float)u);
+                        ll = __float2half_rn((float)(u - (double)__half2float(hh)));
+                    } else {
+                        bad = 1;
                     }
-                    hv[j] = hh;
-                    lv[j] = ll;
                 }
-                dh[k8] = *reinterpret_cast<const uint4 *>(hv);
-                dl[k8] = *reinterpret_cast<const uint4 *>(lv);
+                hv[j] = hh;
+                lv[j] = ll;
             }
+            dh[k8] = *reinterpret_cast<const uint4 *>(hv);
+            dl[k8] = *reinterpret_cast<const uint4 *>(lv);
         }
-        // the pair's lanes add their slices (and combine their out-of-range flags)
-#pragma unroll
-        for (int o = 1; o < LPP; o <<= 1) {
-            s2[0] += __shfl_xor_sync(0xffffffffu, s2[0], o);
-            s2[1] += __shfl_xor_sync(0xffffffffu, s2[1], o);
-            bad[0] |= __shfl_xor_sync(0xffffffffu, bad[0], o);
-            bad[1] |= __shfl_xor_sync(0xffffffffu, bad[1], o);
-        }
+        s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, 1);
         if (part == 0) {
-            unorm[qa] = ra ? sqrtf(s2[0]) : 0.f;
-            unorm[qb] = rb ? sqrtf(s2[1]) : 0.f;
-            if (bad[0]) qbad[qa] = 1;
-            if (bad[1]) qbad[qb] = 1;
+            unorm[q] = real ? sqrtf(s2) : 0.f;
+            if (bad) qbad[q] = 1;
         }
     }
-    // the queries' slices as packed pairs (query 2p in the low half, 2p + 1 in the high),
-    // read from shared memory after a coalesced copy of 64 query rows at a time
-    uint64_t qp[CPT];
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        const int64_t r0 = q0 + 64 * h;
-        for (int e = threadIdx.x; e < 64 * KP; e += RG::THREADS) {
-            const int r = e / KP, k = e % KP;
-            sq[r * (KP + 1) + k] = (r0 + r < m && k < d) ? Q[(r0 + r) * d + k] : 0.f;
-        }
-        __syncthreads();
-        if ((2 * pair) / 64 == h) {
-            const int la = 2 * pair - 64 * h;
-#pragma unroll
-            for (int k = 0; k < CPT; ++k)
-                qp[k] = f2::pack(sq[la * (KP + 1) + k0 + k], sq[(la + 1) * (KP + 1) + k0 + k]);
-        }
-        __syncthreads();
-    }
+    const int wq = warp & 3, wt = warp >> 2, lq = lane & 3, lt = lane >> 2;
+    const int qo = wq * 32 + lq * 8;  // first of the thread's 8 queries (block-relative)
+    const int to = wt * 32 + lt * 4;  // first of its 4 tiles (chunk-relative)
+    // centre slots: the pairs (to, to+1) of a warp's lanes side by side, then (to+2, to+3)
+    const int cs0 = wt * 32 + lt * 2, cs1 = cs0 + 16;
     const int64_t ta = (int64_t)blockIdx.y * tiles_per_block;
     const int64_t tb = min(T, ta + tiles_per_block);
     // upper bound on the exponent -c ||q - x||^2 over the tiles of this block: every x of
     // tile t lies within the tile's max radius rho_t of c_t, so
     //     -c ||q - x||^2 <= -( max(0, sqrt(c R') - sqrt(c) rho_t) )^2,  R' = ||q - c_t||^2
     const float sqc = sqrtf(c);
-    float ubest_a = -INFINITY, ubest_b = -INFINITY;
+    float ubest[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ubest[i] = -INFINITY;
+    // the block's queries, transposed (rows read coordinate-fast; padding: 0)
+    for (int e = tid; e < KP * 128; e += RG::THREADS) {
+        const int r = e / KP, k = e % KP;
+        const int64_t q = q0 + r;
+        sq[k * QS + r] = (q < m && k < d) ? Q[q * d + k] : 0.f;
+    }
     for (int64_t g0 = ta; g0 < tb; g0 += TG) {
         const int gn = (int)min((int64_t)TG, tb - g0);
-        if (g0 > ta) __syncthreads();
-        for (int e = threadIdx.x; e < gn * KP; e += RG::THREADS) {
-            const float cv = cent[(g0 + e / KP) * KP + e % KP];
-            sc[e / KP][e % KP] = f2::pack(cv, cv);
+        uint64_t tot[4][4];  // [tile][query pair], packed (query 2p, 2p+1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) tot[j][p] = 0;
+#pragma unroll 1
+        for (int kb = 0; kb < KP; kb += KC) {
+            __syncthreads();  // the previous block's centres have been read
+            for (int e = tid; e < KC * TG; e += RG::THREADS) {
+                const int j = e % TG, k = e / TG;  // tile j of the chunk, coordinate kb + k
+                const float v = j < gn ? centT[(int64_t)(kb + k) * T + g0 + j] : 0.f;
+                const int jw = j >> 5, jj = j & 31;
+                const int slot = jw * 32 + ((jj & 3) >> 1) * 16 + (jj >> 2) * 2 + (jj & 1);
+                sc[k * TG + slot] = f2::pack(v, v);
+            }
+            if (kb == 0 && tid < TG) srad[tid] = tid < gn ? tinfo[(g0 + tid) * 4 + 1] : 0.f;
+            __syncthreads();
+            uint64_t acc[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) acc[j][p] = 0;
+#pragma unroll
+            for (int k = 0; k < KC; ++k) {
+                const ulonglong2 qa = *reinterpret_cast<const ulonglong2 *>(&sq[(kb + k) * QS + qo]);
+                const ulonglong2 qb = *reinterpret_cast<const ulonglong2 *>(&sq[(kb + k) * QS + qo + 4]);
+                const ulonglong2 ca = *reinterpret_cast<const ulonglong2 *>(&sc[k * TG + cs0]);
+                const ulonglong2 cb = *reinterpret_cast<const ulonglong2 *>(&sc[k * TG + cs1]);
+                const uint64_t qv[4] = {qa.x, qa.y, qb.x, qb.y};
+                const uint64_t cv[4] = {ca.x, ca.y, cb.x, cb.y};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const uint64_t df = f2::sub(qv[p], cv[j]);
+                        acc[j][p] = f2::fma(df, df, acc[j][p]);
+                    }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int p = 0; p < 4; ++p) tot[j][p] = kb == 0 ? acc[j][p] : f2::add(tot[j][p], acc[j][p]);
         }
-        for (int e = threadIdx.x; e < gn; e += RG::THREADS) srad[e] = tinfo[(g0 + e) * 4 + 1];
-        __syncthreads();
-        for (int j = 0; j < gn; ++j) {
-            uint64_t acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;  // {0.f, 0.f}: four chains
+        // row terms (padding queries: 0) and the bounds
 #pragma unroll
-            for (int k = 0; k < CPT; k += 4) {
-                const ulonglong2 c01 = *reinterpret_cast<const ulonglong2 *>(&sc[j][k0 + k]);
-                const ulonglong2 c23 = *reinterpret_cast<const ulonglong2 *>(&sc[j][k0 + k + 2]);
-                const uint64_t d0 = f2::sub(qp[k], c01.x);
-                const uint64_t d1 = f2::sub(qp[k + 1], c01.y);
-                const uint64_t d2 = f2::sub(qp[k + 2], c23.x);
-                const uint64_t d3 = f2::sub(qp[k + 3], c23.y);
-                acc0 = f2::fma(d0, d0, acc0);
-                acc1 = f2::fma(d1, d1, acc1);
-                acc2 = f2::fma(d2, d2, acc2);
-                acc3 = f2::fma(d3, d3, acc3);
-            }
-            float sa, sb;
-            f2::unpack(f2::add(f2::add(acc0, acc1), f2::add(acc2, acc3)), sa, sb);
+        for (int j = 0; j < 4; ++j) {
+            const int jt = to + j;
+            if (jt >= gn) continue;
+            float rv[8];
 #pragma unroll
-            for (int o = 1; o < LPP; o <<= 1) {
-                sa += __shfl_xor_sync(0xffffffffu, sa, o);
-                sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            for (int p = 0; p < 4; ++p) f2::unpack(tot[j][p], rv[2 * p], rv[2 * p + 1]);
+            const float rr = sqc * srad[jt];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                rv[i] = q0 + qo + i < m ? c * rv[i] : 0.f;
+                // slack of 1e-5 relative (far above the approximate square root's ~2^-22
+                // error and the FP32 rounding of the exponents) so that the bound holds
+                const float g = fmaxf(0.f, ptx::sqrt_approx(rv[i]) * (1.f - 1e-5f) - rr);
+                ubest[i] = fmaxf(ubest[i], -g * g);
             }
-            const float cra = c * sa, crb = c * sb;
-            if (part == 0)
-                *reinterpret_cast<float2 *>(&R[(g0 + j) * m_pad + qa]) = make_float2(ra ? cra : 0.f, rb ? crb : 0.f);
-            // slack of 1e-5 relative (far above the approximate square root's ~2^-22 error
-            // and the FP32 rounding of the exponents) so that the bound holds
-            const float rr = sqc * srad[j];
-            const float ga = fmaxf(0.f, ptx::sqrt_approx(cra) * (1.f - 1e-5f) - rr);
-            const float gb = fmaxf(0.f, ptx::sqrt_approx(crb) * (1.f - 1e-5f) - rr);
-            ubest_a = fmaxf(ubest_a, -ga * ga);
-            ubest_b = fmaxf(ubest_b, -gb * gb);
+            float4 *dst = reinterpret_cast<float4 *>(R + (g0 + jt) * m_pad + q0 + qo);
+            dst[0] = make_float4(rv[0], rv[1], rv[2], rv[3]);
+            dst[1] = make_float4(rv[4], rv[5], rv[6], rv[7]);
         }
     }
-    if (tb > ta && part == 0) {
-        atomicMax(ub + qa, float_order_bits(ra ? ubest_a : 0.f));
-        atomicMax(ub + qb, float_order_bits(rb ? ubest_b : 0.f));
+    // the lanes holding the same queries (lane bits 2..4) combine their bounds
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        ubest[i] = fmaxf(ubest[i], __shfl_xor_sync(0xffffffffu, ubest[i], 4));
+        ubest[i] = fmaxf(ubest[i], __shfl_xor_sync(0xffffffffu, ubest[i], 8));
+        ubest[i] = fmaxf(ubest[i], __shfl_xor_sync(0xffffffffu, ubest[i], 16));
+    }
+    if (tb > ta && lt == 0) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int64_t q = q0 + qo + i;
+            atomicMax(ub + q, float_order_bits(q < m ? ubest[i] : 0.f));
+        }
     }
 }
 
@@ -1366,7 +1432,75 @@ int launch_tc_any(int Kp, int eg, const TcInst &inst0, const TcInst *table, int 
     return fail(STAG_KDE_EUNSUPPORTED, "tensor-core form: unsupported operand width");
 }
 
+template <int EG>
+int launch_multi_eg(const TcMulti &mp, int grid, int *err, uint64_t wait_ns, cudaStream_t s) {
+    const uint64_t stall_ns = injected_stall_ns();
+    // the largest shared-memory layout of the four widths (and one CTA per SM at most)
+    constexpr int smem = std::max({Cfg<16, 256, 4, 8, 2, EG>::SMEM, Cfg<32, 256, 4, 8, 2, EG>::SMEM,
+                                   Cfg<64, 256, 2, 8, 1, EG>::SMEM, Cfg<128, 128, 2, 8, 1, EG>::SMEM, 118 * 1024});
+    static_assert(smem <= 232448, "shared memory budget");
+    auto kern = kde_tc_multi_kernel<EG>;
+    // set once per instantiation (before any stream capture can be in progress)
+    static cudaError_t attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    STAG_CUDA_TRY(attr);
+    count_launch();
+    kern<<<grid, 64 + 128 * EG, smem, s>>>(mp, err, wait_ns, stall_ns);
+    STAG_CUDA_TRY(cudaGetLastError());
+    return 0;
+}
+
 }  // namespace
+
+int tc_launch_multi(int eg, const void *const tables[4], const int n_inst[4], const int64_t units[4],
+                    const double work[4], int *err, int sm_count, uint64_t wait_ns, cudaStream_t s) {
+    // CTAs per width in proportion to its work, at least one for a width with units and
+    // never more than its units
+    TcMulti mp{};
+    int cta[4] = {0, 0, 0, 0};
+    double wsum = 0.0;
+    for (int c = 0; c < 4; ++c)
+        if (n_inst[c] > 0 && units[c] > 0) wsum += std::max(work[c], 1e-30);
+    if (wsum <= 0.0) return 0;
+    int total = 0;
+    for (int c = 0; c < 4; ++c) {
+        if (n_inst[c] <= 0 || units[c] <= 0) continue;
+        const double share = sm_count * std::max(work[c], 1e-30) / wsum;
+        cta[c] = (int)std::min<int64_t>(units[c], std::max<int64_t>(1, (int64_t)share));
+        total += cta[c];
+    }
+    while (total > sm_count) {  // more widths than SMs would need: trim the largest
+        int big = 0;
+        for (int c = 1; c < 4; ++c)
+            if (cta[c] > cta[big]) big = c;
+        if (cta[big] <= 1) break;
+        --cta[big];
+        --total;
+    }
+    while (total < sm_count) {  // hand the rest to the width with the most work per CTA
+        int best = -1;
+        double bw = 0.0;
+        for (int c = 0; c < 4; ++c) {
+            if (cta[c] == 0 || cta[c] >= units[c]) continue;
+            const double w = std::max(work[c], 1e-30) / cta[c];
+            if (w > bw) {
+                bw = w;
+                best = c;
+            }
+        }
+        if (best < 0) break;
+        ++cta[best];
+        ++total;
+    }
+    mp.cta_begin[0] = 0;
+    for (int c = 0; c < 4; ++c) {
+        mp.table[c] = reinterpret_cast<const TcInst *>(tables[c]);
+        mp.n_inst[c] = cta[c] > 0 ? n_inst[c] : 0;
+        mp.units[c] = cta[c] > 0 ? units[c] : 0;
+        mp.cta_begin[c + 1] = mp.cta_begin[c] + cta[c];
+    }
+    if (total <= 0) return 0;
+    return eg == 2 ? launch_multi_eg<2>(mp, total, err, wait_ns, s) : launch_multi_eg<4>(mp, total, err, wait_ns, s);
+}
 
 bool tc_supported(int64_t d) { return kp_for(d) != 0; }
 
@@ -1383,6 +1517,7 @@ void tc_free(stag_kde *h) {
         cudaFree(tc->a_aug);
         cudaFree(tc->tinfo);
         cudaFree(tc->cent);
+        cudaFree(tc->centT);
         cudaFree(tc->cg);
         cudaFree(tc->xkt);
         cudaFree(tc->tsum);
@@ -1425,6 +1560,7 @@ int tc_make_view(const stag_kde *base, stag_kde *view) {
     tc->a_aug = b->a_aug;
     tc->tinfo = b->tinfo;
     tc->cent = b->cent;
+    tc->centT = b->centT;
     tc->cg = b->cg;
     tc->xkt = b->xkt;
     tc->tsum = b->tsum;
@@ -1458,6 +1594,7 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     STAG_CUDA_TRY(dev_malloc(&tc->tinfo, tc->T * 4 * sizeof(float)));
     STAG_CUDA_TRY(dev_malloc(&tc->cent, tc->T * Kp * sizeof(float)));
     STAG_CUDA_TRY(dev_malloc(&tc->cg, Kp * sizeof(float)));
+    STAG_CUDA_TRY(dev_malloc(&tc->centT, tc->T * Kp * sizeof(float)));
     // the recompute of flagged queries reads the points in tile (k-d) order, in the plain
     // form's tile-transposed layout
     if (h->tc_check) {
@@ -1487,6 +1624,8 @@ int tc_prepare_points(stag_kde *h, const float *dX) {
     tc_split_points_kernel<<<grid_for(tc->n_pad, 128), 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->n_pad, tc->cent,
                                                                     tc->cg, tc->scales, tc->b_hi, tc->b_lo, tc->b_aug);
     tc_tile_radius_kernel<<<(unsigned)tc->T, 128, 0, s>>>(dX, h->n, h->d, tc->BN, Kp, tc->cent, tc->tinfo);
+    count_launch();
+    tc_transpose_centres_kernel<<<grid_for(tc->T * Kp, 256), 256, 0, s>>>(tc->cent, tc->T, Kp, tc->centT);
     STAG_CUDA_TRY(cudaGetLastError());
     int rc = make_map(&tc->map_bhi, tc->b_hi, tc->n_pad, Kp, tc->BN);
     if (!rc) rc = make_map(&tc->map_blo, tc->b_lo, tc->n_pad, Kp, tc->BN);
@@ -1647,16 +1786,21 @@ static int tc_prep(stag_kde *h, const float *dQ, int64_t m, cudaStream_t s) {
     count_launch(1);
     // tiles per block: 256, fewer when that leaves under ~4 blocks per SM (small batches)
     int tpb = 256;
-    while (tpb > 8 && (m_pad / BM) * ceil_div(tc->T, tpb) < 4 * (int64_t)h->sm_count) tpb /= 2;
+    while (tpb > RowTermGeo::TG && (m_pad / BM) * ceil_div(tc->T, tpb) < 4 * (int64_t)h->sm_count) tpb /= 2;
     dim3 grid((unsigned)(m_pad / BM), (unsigned)ceil_div(tc->T, tpb));
     switch (Kp) {
 #define STAG_ROWTERM(KPV)                                                                                          \
-    case KPV:                                                                                                      \
-        tc_rowterm_kernel<KPV><<<grid, RowTermGeo<KPV>::THREADS, 0, s>>>(dQ, m, h->d, m_pad, tc->cent, tc->T, tpb,   \
-                                                                         (float)c, tc->rowterm,                   \
-                                                    tc->cg, tc->unorm, tc->tinfo, tc->ub, tc->scales, tc->a_hi,    \
-                                                    tc->a_lo, tc->qbad);                                           \
-        break;
+    case KPV: {                                                                                                    \
+        /* set once per instantiation (before any stream capture can be in progress) */                           \
+        static cudaError_t attr = cudaFuncSetAttribute(tc_rowterm_kernel<KPV>,                                    \
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,               \
+                                                       RowTermGeo::smem_bytes(KPV));                              \
+        STAG_CUDA_TRY(attr);                                                                                       \
+        tc_rowterm_kernel<KPV><<<grid, RowTermGeo::THREADS, RowTermGeo::smem_bytes(KPV), s>>>(                     \
+            dQ, m, h->d, m_pad, tc->cent, tc->T, tpb, (float)c, tc->rowterm, tc->cg, tc->unorm, tc->tinfo, tc->ub,  \
+            tc->scales, tc->a_hi, tc->a_lo, tc->qbad, tc->centT);                                                  \
+        break;                                                                                                     \
+    }
         STAG_ROWTERM(16)
         STAG_ROWTERM(32)
         STAG_ROWTERM(64)
@@ -1767,13 +1911,6 @@ int64_t tc_fill_inst(const stag_kde *h, int64_t m, int tiles_per_unit, int64_t u
     TcInst *I = reinterpret_cast<TcInst *>(inst);
     fill_inst(h, m, q_tiles, *splits, tps, unit_begin, I);
     return I->units;
-}
-
-int tc_launch_table(int Kp, int eg, const void *table, int n_inst, int64_t total_units, int *err, int sm_count,
-                    uint64_t wait_ns, cudaStream_t s) {
-    static TcInst unused{};  // kernel parameter slot; the kernel reads the table
-    return launch_tc_any(Kp, eg, unused, reinterpret_cast<const TcInst *>(table), n_inst, total_units, err, sm_count,
-                         wait_ns, s);
 }
 
 int tc_finish_public(stag_kde *h, const float *dQ, int64_t m, int64_t splits, double *dOut, cudaStream_t s) {

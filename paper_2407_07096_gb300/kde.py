@@ -193,8 +193,8 @@ class ExactGaussianKDE:
 
 def query_batch(kdes, Qs, outs=None, stream=None):
     """Evaluates ``Qs[i]`` (contiguous CUDA tensors) against ``kdes[i]`` in one batched
-    call (one persistent tensor-core launch per operand width, replayed from a captured
-    CUDA graph on repeated calls with the same tensors). Returns the output tensors."""
+    call (one persistent tensor-core launch serving every operand width, replayed from a
+    captured CUDA graph on repeated calls with the same tensors). Returns the output tensors."""
     import torch
     lib = L.load()
     n = len(kdes)
