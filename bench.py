@@ -310,7 +310,7 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-KERNEL_REGION = ("__global__ void __launch_bounds__(64 + 128 * EG, 1)",
+KERNEL_REGION = ("__device__ __forceinline__ void tc_body(",
                  "// ------------------------------------------------------------------ prep kernels")
 
 

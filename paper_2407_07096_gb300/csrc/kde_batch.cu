@@ -58,7 +58,7 @@ struct BatchPlan {
     // side streams: the instances' preparation and finish chains are spread over them so
     // that the small kernels of different instances overlap on the device (in the graph
     // they become parallel branches between a fork and a join event)
-    static constexpr int kSide = 8;
+    static constexpr int kSide = 32;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork = nullptr, joined[kSide] = {};
     cudaGraph_t graph = nullptr;

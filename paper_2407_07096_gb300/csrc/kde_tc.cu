@@ -210,6 +210,8 @@ __device__ __forceinline__ const TcInst *find_inst(const TcInst *insts, int n_in
     return insts + lo;
 }
 
+__device__ __forceinline__ int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
 __device__ __forceinline__ int cexp(float e) { return (int)fminf(fmaxf(e, -4000.f), 4000.f); }
 
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
@@ -1044,52 +1046,70 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
         const int64_t q = q0 + r;
         sq[k * QS + r] = (q < m && k < d) ? Q[q * d + k] : 0.f;
     }
-    for (int64_t g0 = ta; g0 < tb; g0 += TG) {
+    // Stages: (chunk of 64 tiles, block of 16 coordinates). The centres (and, at a chunk's
+    // first block, the tiles' radii) of the next stage are loaded into registers while the
+    // current stage is computed, so the global-memory latency hides behind the math.
+    constexpr int NKB = KP / KC, PER = KC * TG / RG::THREADS;  // values a thread stages
+    const int nstages = (int)ceil_div_dev(tb - ta, (int64_t)TG) * NKB;
+    float pv[PER], prad = 0.f;
+    auto load_stage = [&](int st) {
+        const int64_t g0 = ta + (int64_t)(st / NKB) * TG;
+        const int kb = (st % NKB) * KC;
         const int gn = (int)min((int64_t)TG, tb - g0);
-        uint64_t tot[4][4];  // [tile][query pair], packed (query 2p, 2p+1)
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = tid + i * RG::THREADS;
+            const int j = e % TG, k = e / TG;  // tile j of the chunk, coordinate kb + k
+            pv[i] = j < gn ? centT[(int64_t)(kb + k) * T + g0 + j] : 0.f;
+        }
+        prad = (kb == 0 && tid < gn) ? tinfo[(g0 + tid) * 4 + 1] : 0.f;
+    };
+    if (nstages > 0) load_stage(0);
+    uint64_t tot[4][4];  // [tile][query pair], packed (query 2p, 2p+1)
+#pragma unroll 1
+    for (int st = 0; st < nstages; ++st) {
+        const int64_t g0 = ta + (int64_t)(st / NKB) * TG;
+        const int kb = (st % NKB) * KC;
+        const int gn = (int)min((int64_t)TG, tb - g0);
+        __syncthreads();  // the previous stage's centres (and radii) have been read
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = tid + i * RG::THREADS;
+            const int j = e % TG, k = e / TG;
+            const int jw = j >> 5, jj = j & 31;
+            const int slot = jw * 32 + ((jj & 3) >> 1) * 16 + (jj >> 2) * 2 + (jj & 1);
+            sc[k * TG + slot] = f2::pack(pv[i], pv[i]);
+        }
+        if (kb == 0 && tid < TG) srad[tid] = prad;
+        __syncthreads();
+        if (st + 1 < nstages) load_stage(st + 1);
+        uint64_t acc[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
 #pragma unroll
-            for (int p = 0; p < 4; ++p) tot[j][p] = 0;
-#pragma unroll 1
-        for (int kb = 0; kb < KP; kb += KC) {
-            __syncthreads();  // the previous block's centres have been read
-            for (int e = tid; e < KC * TG; e += RG::THREADS) {
-                const int j = e % TG, k = e / TG;  // tile j of the chunk, coordinate kb + k
-                const float v = j < gn ? centT[(int64_t)(kb + k) * T + g0 + j] : 0.f;
-                const int jw = j >> 5, jj = j & 31;
-                const int slot = jw * 32 + ((jj & 3) >> 1) * 16 + (jj >> 2) * 2 + (jj & 1);
-                sc[k * TG + slot] = f2::pack(v, v);
-            }
-            if (kb == 0 && tid < TG) srad[tid] = tid < gn ? tinfo[(g0 + tid) * 4 + 1] : 0.f;
-            __syncthreads();
-            uint64_t acc[4][4];
+            for (int p = 0; p < 4; ++p) acc[j][p] = 0;
+#pragma unroll
+        for (int k = 0; k < KC; ++k) {
+            const ulonglong2 qa = *reinterpret_cast<const ulonglong2 *>(&sq[(kb + k) * QS + qo]);
+            const ulonglong2 qb = *reinterpret_cast<const ulonglong2 *>(&sq[(kb + k) * QS + qo + 4]);
+            const ulonglong2 ca = *reinterpret_cast<const ulonglong2 *>(&sc[k * TG + cs0]);
+            const ulonglong2 cb = *reinterpret_cast<const ulonglong2 *>(&sc[k * TG + cs1]);
+            const uint64_t qv[4] = {qa.x, qa.y, qb.x, qb.y};
+            const uint64_t cv[4] = {ca.x, ca.y, cb.x, cb.y};
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
-                for (int p = 0; p < 4; ++p) acc[j][p] = 0;
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                const ulonglong2 qa = *reinterpret_cast<const ulonglong2 *>(&sq[(kb + k) * QS + qo]);
-                const ulonglong2 qb = *reinterpret_cast<const ulonglong2 *>(&sq[(kb + k) * QS + qo + 4]);
-                const ulonglong2 ca = *reinterpret_cast<const ulonglong2 *>(&sc[k * TG + cs0]);
-                const ulonglong2 cb = *reinterpret_cast<const ulonglong2 *>(&sc[k * TG + cs1]);
-                const uint64_t qv[4] = {qa.x, qa.y, qb.x, qb.y};
-                const uint64_t cv[4] = {ca.x, ca.y, cb.x, cb.y};
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const uint64_t df = f2::sub(qv[p], cv[j]);
-                        acc[j][p] = f2::fma(df, df, acc[j][p]);
-                    }
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int p = 0; p < 4; ++p) tot[j][p] = kb == 0 ? acc[j][p] : f2::add(tot[j][p], acc[j][p]);
+                for (int p = 0; p < 4; ++p) {
+                    const uint64_t df = f2::sub(qv[p], cv[j]);
+                    acc[j][p] = f2::fma(df, df, acc[j][p]);
+                }
         }
-        // row terms (padding queries: 0) and the bounds
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int p = 0; p < 4; ++p) tot[j][p] = kb == 0 ? acc[j][p] : f2::add(tot[j][p], acc[j][p]);
+        if (kb + KC < KP) continue;
+        // the chunk's row terms (padding queries: 0) and the bounds
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int jt = to + j;

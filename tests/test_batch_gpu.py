@@ -1,5 +1,6 @@
 """The batched path (stag_kde_query_batch): instances of uneven n, m, d and a through one
-persistent tensor-core launch per operand width, captured in a CUDA graph. Every result
+persistent tensor-core launch serving every operand width (a CTA range per width), captured
+in a CUDA graph. Every result
 must equal a solo query on the same handle within the form's tolerance, and match the
 FP64 oracle; replays must be bitwise identical and see new query contents."""
 
@@ -36,7 +37,8 @@ def lib():
 def test_batch_matches_solo_and_oracle(lib):
     import torch
     from paper_2407_07096_gb300.kde import ExactGaussianKDE, query_batch
-    inst = make_instances(13)
+    # every operand width (16, 32, 64, 128) in the one launch
+    inst = make_instances(13, dims=(8, 32, 128, 64))
     kdes = [ExactGaussianKDE(X, a) for X, _, a in inst]
     # one plain-form instance in the same batch
     X, Q, a = inst[0]
