@@ -71,10 +71,10 @@ struct TcData {
     __half *b_hi = nullptr, *b_lo = nullptr;  // [n_pad][Kp]
     __half *b_aug = nullptr;                  // [n_pad][16]: -g / (2 scale) in 3 FP16 pieces, then 0
     __half *a_aug = nullptr;                  // [128][16]: s_a, s_a, s_a, 0, ...
-    float *tinfo = nullptr;                   // [T][4]: RMS radius, max radius rounded up to bound
-                                              //         FP32 distances (exponent bounds), max radius,
-                                              //         the error estimate's accumulation weight
-                                              //         FP32 distances), 0, 0
+    float *tinfo = nullptr;                   // [T][4]: RMS radius (the error estimate's split
+                                              //         term), max radius rounded up so that it bounds
+                                              //         FP32 distances (exponent bounds, pruning), max
+                                              //         radius, the estimate's accumulation weight
     float *cent = nullptr;                    // [T][Kp]: tile centres c_t (FP32)
     float *centT = nullptr;                   // [Kp][T]: the same, coordinate-major (row terms)
     float *cg = nullptr;                      // [Kp]: global centre c_g
