@@ -50,6 +50,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <climits>
 #include <type_traits>
 #include <mutex>
 
@@ -1083,6 +1084,7 @@ tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_p
         if (kb == 0 && tid < TG) srad[tid] = prad;
         __syncthreads();
         if (st + 1 < nstages) load_stage(st + 1);
+        if (to >= gn) continue;  // all four of this thread's tiles lie past the range's end
         uint64_t acc[4][4];
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -1209,8 +1211,7 @@ tc_scan_kernel(const int *__restrict__ in, const int *__restrict__ cnt_dev, int 
 
 // The flagged queries in query order (block b's flagged queries start at boff[b]; inside
 // a block, by warp, then lane), each with the tile holding the lower bound LB of its
-// largest exponent as sort key, and its threshold LB - 64. One thread per query: the row
-// terms of 32 consecutive queries are read together, tile by tile.
+// largest exponent as sort key, and its threshold LB - 64.
 __global__ void __launch_bounds__(256)
 tc_flag_compact_kernel(const int *__restrict__ qflag, const int *__restrict__ boff, int64_t m, int64_t m_pad,
                        const float *__restrict__ R, const float *__restrict__ tinfo, int64_t T, float c,
@@ -1224,36 +1225,52 @@ tc_flag_compact_kernel(const int *__restrict__ qflag, const int *__restrict__ bo
     if (lane == 0) wcnt[warp] = __popc(mask);
     __syncthreads();
     if (!mask) return;
-    int w = boff[blockIdx.x] + __popc(mask & ((1u << lane) - 1u));
-    for (int k = 0; k < warp; ++k) w += wcnt[k];
+    int w0 = boff[blockIdx.x];
+    for (int k = 0; k < warp; ++k) w0 += wcnt[k];
     const float sqc = sqrtf(c);
-    float best = -INFINITY;
-    int bt = 0;
-    if (flag) {
-        // eight row terms in flight per thread (the loads of a warp's 32 queries coalesce)
-        constexpr int U = 8;
-        for (int t0 = 0; t0 < (int)T; t0 += U) {
-            float rv[U], rho[U];
+    // the warp takes its flagged queries one at a time, its lanes striding over the tiles
+    // (four row terms in flight per lane), then a warp arg-max (ties keep the smaller tile)
+    unsigned rem = mask;
+    while (rem) {
+        const int src = __ffs(rem) - 1;
+        rem &= rem - 1u;
+        const int64_t jq = blockIdx.x * (int64_t)blockDim.x + warp * 32 + src;
+        float best = -INFINITY;
+        int bt = INT_MAX;
+        for (int t0 = lane; t0 < (int)T; t0 += 4 * 32) {
+            float rv[4], rho[4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int t = min(t0 + u, (int)T - 1);
-                rv[u] = R[(int64_t)t * m_pad + j];
+            for (int u = 0; u < 4; ++u) {
+                const int t = min(t0 + 32 * u, (int)T - 1);
+                rv[u] = R[(int64_t)t * m_pad + jq];
                 rho[u] = tinfo[(int64_t)t * 4 + 1];
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 const float h2 = sqrtf(rv[u]) * (1.f + 1e-5f) + sqc * rho[u];
                 const float lb = -h2 * h2;
-                if (t0 + u < (int)T && lb > best) {  // ties keep the smaller tile
+                if (t0 + 32 * u < (int)T && lb > best) {  // a lane's tiles ascend
                     best = lb;
-                    bt = t0 + u;
+                    bt = t0 + 32 * u;
                 }
             }
         }
-        fix_idx[w] = (int)j;
-        key[w] = (uint64_t)bt;
-        val[w] = (uint32_t)j;
-        thr[j] = best - kPruneLog2;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+            const int ot = __shfl_xor_sync(0xffffffffu, bt, off);
+            if (ob > best || (ob == best && ot < bt)) {
+                best = ob;
+                bt = ot;
+            }
+        }
+        if (lane == src) {
+            const int w = w0 + __popc(mask & ((1u << src) - 1u));
+            fix_idx[w] = (int)jq;
+            key[w] = (uint64_t)bt;
+            val[w] = (uint32_t)jq;
+            thr[jq] = best - kPruneLog2;
+        }
     }
 }
 
@@ -1286,9 +1303,16 @@ tc_group_keep_kernel(const uint32_t *__restrict__ order, const float *__restrict
             bool keep = false;
             if (t < T) {
                 const float rho = sqc * tinfo[t * 4 + 1];
-                for (int r = 0; r < rows && !keep; ++r) {
-                    const float gap = fmaxf(0.f, sqrtf(R[t * m_pad + sq[r]]) * (1.f - 1e-5f) - rho);
-                    keep = -gap * gap >= sthr[r];
+                // eight members' row terms in flight at a time
+                for (int r0 = 0; r0 < rows && !keep; r0 += 8) {
+                    float rv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) rv[u] = R[t * m_pad + sq[min(r0 + u, rows - 1)]];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float gap = fmaxf(0.f, sqrtf(rv[u]) * (1.f - 1e-5f) - rho);
+                        keep = keep || (r0 + u < rows && -gap * gap >= sthr[r0 + u]);
+                    }
                 }
             }
             const unsigned mask = __ballot_sync(0xffffffffu, keep);
