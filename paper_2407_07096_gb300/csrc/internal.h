@@ -32,6 +32,11 @@ int cuda_fail(cudaError_t e, const char *what);
 // ---------------------------------------------------------------------------------
 constexpr int kSimtTile = 64;  // rows per tile (queries per block, points per tile)
 constexpr int kSimtKC = 32;    // coordinates per shared-memory chunk
+// Up to this d_pad the plain form keeps a block's whole query tile in shared memory
+// (d_pad x 64 floats, 32 KB at 128) and streams only the point chunks; beyond it the
+// query tile is streamed chunk by chunk beside the points.
+constexpr int kSimtResidentMaxD = 128;
+inline size_t simt_resident_bytes(int d_pad) { return (size_t)d_pad * kSimtTile * sizeof(float); }
 
 // Every device allocation of the library goes through dev_malloc. It is also the
 // library's host-side fault-injection point: while the environment variable

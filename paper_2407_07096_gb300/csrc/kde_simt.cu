@@ -109,7 +109,7 @@ __device__ __forceinline__ void merge(RowAcc &r, double oacc, float oshift) {
 // tiles, tile_at(i) giving the index of the i-th. Rows at or past rows_valid are
 // computed on zero padding and not stored; the partials of row r go to out_sum[r] and
 // out_shift[r].
-template <bool kSingleChunk, int KERN, class TileAt>
+template <bool kQResident, int KERN, class TileAt>
 __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], float (*sQ)[kSimtKC * kSimtTile],
                                           const float *__restrict__ xt, int64_t n, const float *__restrict__ qbase,
                                           int d_pad, float negc, int64_t ntiles, TileAt tile_at, int64_t rows_valid,
@@ -129,13 +129,13 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
         const int nvec = klen * (kSimtTile / 4);
         const float *src = xt + (t * d_pad + k0) * kSimtTile;
         for (int v = tid; v < nvec; v += 256) cp_async16(&sX[stage][v * 4], src + v * 4);
-        if (!kSingleChunk) {
+        if (!kQResident) {
             const float *qs = qbase + (int64_t)k0 * kSimtTile;
-            for (int v = tid; v < nvec; v += 256) cp_async16(&sQ[kSingleChunk ? 0 : stage][v * 4], qs + v * 4);
+            for (int v = tid; v < nvec; v += 256) cp_async16(&sQ[kQResident ? 0 : stage][v * 4], qs + v * 4);
         }
     };
 
-    if (kSingleChunk) {
+    if (kQResident) {
         const int nvec = d_pad * (kSimtTile / 4);
         for (int v = tid; v < nvec; v += 256) cp_async16(&sQ[0][v * 4], qbase + v * 4);
     }
@@ -163,7 +163,7 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
         const int ch = (int)(it % nch);
         const int klen = min(kSimtKC, d_pad - ch * kSimtKC);
         const float *xs = sX[stage];
-        const float *qs = kSingleChunk ? sQ[0] + ch * kSimtKC * kSimtTile : sQ[kSingleChunk ? 0 : stage];
+        const float *qs = kQResident ? sQ[0] + ch * kSimtKC * kSimtTile : sQ[kQResident ? 0 : stage];
         // blocks of kSumBlock coordinates: each block's squares are summed in a chain of
         // its own and the block sum is added to the pair's total, which keeps the
         // accumulated rounding error of d2 about half that of one chain over all d
@@ -246,7 +246,7 @@ __device__ __forceinline__ void simt_item(float (*sX)[kSimtKC * kSimtTile], floa
 
 // The contiguous point tiles of split `split` against query tile `qtile`; partials of
 // query q at part_sum[split * m + q] (rows from m_real on are not stored).
-template <bool kSingleChunk, int KERN>
+template <bool kQResident, int KERN>
 __device__ __forceinline__ void simt_split_item(float (*sX)[kSimtKC * kSimtTile], float (*sQ)[kSimtKC * kSimtTile],
                                                 const float *__restrict__ xt, int64_t n, int64_t n_tiles,
                                                 const float *__restrict__ qt, int64_t m, int64_t m_real, int d_pad,
@@ -255,20 +255,25 @@ __device__ __forceinline__ void simt_split_item(float (*sX)[kSimtKC * kSimtTile]
     const int64_t t0 = split * tiles_per_split;
     const int64_t t1 = min(n_tiles, t0 + tiles_per_split);
     const int64_t off = split * m + qtile * kSimtTile;
-    simt_item<kSingleChunk, KERN>(sX, sQ, xt, n, qt + qtile * (int64_t)d_pad * kSimtTile, d_pad, negc,
+    simt_item<kQResident, KERN>(sX, sQ, xt, n, qt + qtile * (int64_t)d_pad * kSimtTile, d_pad, negc,
                                   max((int64_t)0, t1 - t0), [t0](int64_t i) { return t0 + i; },
                                   m_real - qtile * kSimtTile, part_sum + off, part_shift + off);
 }
 
-template <bool kSingleChunk, int KERN>
+template <bool kQResident, int KERN>
 __global__ void __launch_bounds__(256, 2)
 kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, const float *__restrict__ qt, int64_t m,
                     int d_pad, float negc, int64_t tiles_per_split, double *__restrict__ part_sum,
                     float *__restrict__ part_shift) {
     __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
-    __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
+    // resident query tile: all d_pad coordinates (dynamic, d_pad x 64 floats); otherwise
+    // double-buffered chunks of the query tile
+    extern __shared__ __align__(16) float sQres[];
+    __shared__ __align__(16) float sQchunk[kQResident ? 1 : 2][kQResident ? 4 : kSimtKC * kSimtTile];
+    auto sQ = kQResident ? reinterpret_cast<float (*)[kSimtKC * kSimtTile]>(sQres)
+                         : reinterpret_cast<float (*)[kSimtKC * kSimtTile]>(&sQchunk[0][0]);
     // one block per (query tile, split)
-    simt_split_item<kSingleChunk, KERN>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum,
+    simt_split_item<kQResident, KERN>(sX, sQ, xt, n, n_tiles, qt, m, m, d_pad, negc, tiles_per_split, part_sum,
                                         part_shift, blockIdx.x, blockIdx.y);
 }
 
@@ -278,7 +283,7 @@ kde_simt_f32_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, co
 // list kept[g * kstride ..], s = w - item_off[g]; each kept tile is `per` consecutive
 // 64-point tiles of xt. Query group g is tile g of qt (64 gathered rows). The partials of
 // row r go to part_sum[w * 64 + r]. A fixed grid walks the items (counts on the device).
-template <bool kSingleChunk, int KERN>
+template <bool kQResident, int KERN>
 __global__ void __launch_bounds__(256, 2)
 kde_simt_f32_list_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tiles, const float *__restrict__ qt,
                          int d_pad, float negc, const int *__restrict__ kept, int64_t kstride,
@@ -286,7 +291,12 @@ kde_simt_f32_list_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tile
                          const int *__restrict__ n_groups, int seg, int per, double *__restrict__ part_sum,
                          float *__restrict__ part_shift) {
     __shared__ __align__(16) float sX[2][kSimtKC * kSimtTile];
-    __shared__ __align__(16) float sQ[kSingleChunk ? 1 : 2][kSimtKC * kSimtTile];
+    // resident query tile: all d_pad coordinates (dynamic, d_pad x 64 floats); otherwise
+    // double-buffered chunks of the query tile
+    extern __shared__ __align__(16) float sQres[];
+    __shared__ __align__(16) float sQchunk[kQResident ? 1 : 2][kQResident ? 4 : kSimtKC * kSimtTile];
+    auto sQ = kQResident ? reinterpret_cast<float (*)[kSimtKC * kSimtTile]>(sQres)
+                         : reinterpret_cast<float (*)[kSimtKC * kSimtTile]>(&sQchunk[0][0]);
     const int G = *n_groups;
     const int total = G > 0 ? item_off[G] : 0;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
@@ -307,7 +317,7 @@ kde_simt_f32_list_kernel(const float *__restrict__ xt, int64_t n, int64_t n_tile
         // be the list's last entry (the lists ascend), whose tail is enumerated last
         int64_t nt = (int64_t)(k1 - k0) * per;
         if (k1 > k0) nt -= max((int64_t)0, ((int64_t)list[k1 - k0 - 1] + 1) * per - n_tiles);
-        simt_item<kSingleChunk, KERN>(
+        simt_item<kQResident, KERN>(
             sX, sQ, xt, n, qt + (int64_t)g * d_pad * kSimtTile, d_pad, negc, nt,
             [list, per](int64_t i) { return (int64_t)list[i / per] * per + i % per; }, kSimtTile,
             part_sum + (int64_t)w * kSimtTile, part_shift + (int64_t)w * kSimtTile);
@@ -454,8 +464,8 @@ int simt_prepare_points(stag_kde *h, const float *dX) {
 // Launches the FP32 kernel instance for the handle's operand width and kernel function.
 template <int KERN>
 void launch_simt_kern(const stag_kde *h, dim3 grid, cudaStream_t s, int64_t m, float negc, int64_t tps) {
-    if (h->d_pad <= kSimtKC)
-        kde_simt_f32_kernel<true, KERN><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
+    if (h->d_pad <= kSimtResidentMaxD)
+        kde_simt_f32_kernel<true, KERN><<<grid, 256, simt_resident_bytes(h->d_pad), s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
                                                              h->part.sum, h->part.shift);
     else
         kde_simt_f32_kernel<false, KERN><<<grid, 256, 0, s>>>(h->xt, h->n, h->n_tiles, h->qt, m, h->d_pad, negc, tps,
@@ -553,8 +563,8 @@ int simt_list_launch(const stag_kde *h, const float *xt, const float *qt, const 
     const float negc = (float)(-h->a * 1.4426950408889634);  // -a log2(e)
     const dim3 grid((unsigned)(h->sm_count * 2));
     count_launch();
-    if (h->d_pad <= kSimtKC)
-        kde_simt_f32_list_kernel<true, STAG_KDE_KERNEL_GAUSSIAN><<<grid, 256, 0, s>>>(
+    if (h->d_pad <= kSimtResidentMaxD)
+        kde_simt_f32_list_kernel<true, STAG_KDE_KERNEL_GAUSSIAN><<<grid, 256, simt_resident_bytes(h->d_pad), s>>>(
             xt, h->n, h->n_tiles, qt, h->d_pad, negc, kept, kstride, kcount, item_off, n_groups, seg, per, part_sum,
             part_shift);
     else
