@@ -970,7 +970,7 @@ struct RowTermGeo {
 };
 
 template <int KP>
-__global__ void __launch_bounds__(RowTermGeo::THREADS, 2)
+__global__ void __launch_bounds__(RowTermGeo::THREADS, KP <= 16 ? 3 : 2)
 tc_rowterm_kernel(const float *__restrict__ Q, int64_t m, int64_t d, int64_t m_pad, const float *__restrict__ cent,
                   int64_t T, int tiles_per_block, float c, float *__restrict__ R, const float *__restrict__ cg,
                   float *__restrict__ unorm, const float *__restrict__ tinfo, unsigned *__restrict__ ub,
