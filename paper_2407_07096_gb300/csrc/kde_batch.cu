@@ -144,7 +144,7 @@ int build_tables(BatchPlan *p) {
 }
 
 // Queues the whole batch on stream s: the instances' query preparation spread over the
-// side streams, one persistent tensor-core launch per operand width on s, then the
+// side streams, one persistent tensor-core launch for every operand width on s, then the
 // instances' combine and recompute chains spread over the side streams again; s waits
 // for every side stream at the end (fork/join with events, so the order holds both when
 // run directly and when captured into the graph).

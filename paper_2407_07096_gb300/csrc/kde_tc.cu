@@ -1228,8 +1228,42 @@ tc_flag_compact_kernel(const int *__restrict__ qflag, const int *__restrict__ bo
     int w0 = boff[blockIdx.x];
     for (int k = 0; k < warp; ++k) w0 += wcnt[k];
     const float sqc = sqrtf(c);
-    // the warp takes its flagged queries one at a time, its lanes striding over the tiles
-    // (four row terms in flight per lane), then a warp arg-max (ties keep the smaller tile)
+    if (__popc(mask) >= 8) {
+        // many flagged queries in the warp: each lane walks the tiles of its own query
+        // (eight row terms in flight; the loads of the warp's queries coalesce)
+        if (flag) {
+            float best = -INFINITY;
+            int bt = 0;
+            constexpr int U = 8;
+            for (int t0 = 0; t0 < (int)T; t0 += U) {
+                float rv[U], rho[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int t = min(t0 + u, (int)T - 1);
+                    rv[u] = R[(int64_t)t * m_pad + j];
+                    rho[u] = tinfo[(int64_t)t * 4 + 1];
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float h2 = sqrtf(rv[u]) * (1.f + 1e-5f) + sqc * rho[u];
+                    const float lb = -h2 * h2;
+                    if (t0 + u < (int)T && lb > best) {  // ties keep the smaller tile
+                        best = lb;
+                        bt = t0 + u;
+                    }
+                }
+            }
+            const int w = w0 + __popc(mask & ((1u << lane) - 1u));
+            fix_idx[w] = (int)j;
+            key[w] = (uint64_t)bt;
+            val[w] = (uint32_t)j;
+            thr[j] = best - kPruneLog2;
+        }
+        return;
+    }
+    // few: the warp takes its flagged queries one at a time, its lanes striding over the
+    // tiles (four row terms in flight per lane), then a warp arg-max (ties keep the
+    // smaller tile)
     unsigned rem = mask;
     while (rem) {
         const int src = __ffs(rem) - 1;
