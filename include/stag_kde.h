@@ -214,9 +214,10 @@ void stag_lsh_destroy(stag_lsh_t *h);
  * Batched evaluation: instance i evaluates the device query matrix dQs[i] (ms[i] rows,
  * the handle's element type and d) against handle hs[i] into dOuts[i] (ms[i] doubles).
  * The handles must be distinct and live on one device; ms[i] may differ, and so may the
- * handles' n, d and a. Tensor-core instances of the same operand width share ONE
- * persistent kernel launch whose work list spans all their (query tile, point range)
- * units; every instance keeps its own partial sums and FP64 combine, so its results
+ * handles' n, d and a. All tensor-core instances share ONE persistent kernel launch:
+ * its CTAs are split into one range per operand width (sized by the width's share of the
+ * work), and each range walks the (query tile, point range) units of every instance of
+ * its width; every instance keeps its own partial sums and FP64 combine, so its results
  * equal a solo call on the same handle within the form's tolerance.
  * The first call with a given (handles, pointers, sizes) tunes the tensor-core launch
  * settings on the batch, reserves all scratch and captures the whole batch into a CUDA
