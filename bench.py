@@ -612,6 +612,11 @@ def run_gpu(args):
         # the largest single-GPU workload, measured in the same run as a second object
         large = measure(args, "large_d64", lib, dev, world, rank, local, args.steps, args.warmup,
                         not args.no_cpu_baseline, ex2_rate)
+    batched = None
+    if (args.workload == "single_d16" and not args.no_batched and world == 1 and args.n is None
+            and args.m is None):
+        # the batched workload (256 instances, one graph replay per step) as a third object
+        batched = measure_batched(args, args.steps, args.warmup)
     if rank == 0:
         def obj(x, workload):
             return {"value": x["value"], "unit": UNIT, "ms_per_step": x["ms_per_step"],
@@ -631,6 +636,15 @@ def run_gpu(args):
                 "mufu_probe": probe}
         if large:
             line["large_d64"] = obj(large, "large_d64")
+        if batched:
+            line["batched_256"] = {
+                "value": batched["value"], "unit": UNIT, "ms_per_step": batched["ms_per_step"],
+                "config": {"workload": WORKLOADS["batched"], "instances": batched["instances"],
+                           "pairs_per_step": batched["pairs"], "forms": batched["forms"],
+                           "l2": "flushed between steps (512 MiB write)", "parallelism": "one GPU"},
+                **{k: batched[k] for k in ("plan_s", "gpu_launches", "recomputed_fp32_queries",
+                                           "max_rel_err_sampled", "cpu_baseline", "roofline", "clocks",
+                                           "step_ms")}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -874,7 +888,9 @@ def build_batched(count=256, seed=0):
     return inst
 
 
-def run_batched(args):
+def measure_batched(args, steps, warmup, count=256):
+    """One batched call (graph replay) per step over `count` instances of the batched
+    workload; returns the measured numbers (see run_batched)."""
     import torch
     from paper_2407_07096_gb300 import build as B
     from paper_2407_07096_gb300 import _lib as L
@@ -883,7 +899,7 @@ def run_batched(args):
     lib = L.load()
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
-    inst = build_batched(args.count)
+    inst = build_batched(count)
     gen_s = time.perf_counter() - t0
     kdes = [ExactGaussianKDE(X, a, form=args.form) for X, _, a in inst]
     Qs = [torch.from_numpy(Q).to(dev) for _, Q, _ in inst]
@@ -894,7 +910,7 @@ def run_batched(args):
     query_batch(kdes, Qs, outs, stream)  # plan: tune + capture
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         query_batch(kdes, Qs, outs, stream)
     torch.cuda.synchronize()
     if args.profile_one_step:
@@ -904,11 +920,11 @@ def run_batched(args):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     clocks = ClockSampler(0)
     clocks.start()
     l0 = lib.stag_kde_launch_count()
-    for i in range(args.steps):
+    for i in range(steps):
         with torch.cuda.stream(stream):
             flush.zero_()
             ev[i][0].record(stream)
@@ -919,25 +935,59 @@ def run_batched(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    # parity on sampled queries of a few instances
-    import oracle
-    errs = []
-    for i in range(0, len(inst), max(1, len(inst) // 8)):
-        X, Q, a = inst[i]
-        idx = np.arange(0, Q.shape[0], max(1, Q.shape[0] // 16))
-        errs.append(float(np.max(oracle.rel_err(outs[i].cpu().numpy()[idx], oracle.kde(X, Q[idx], a)))))
+    # CPU-baseline leg: the FP64 oracle on sampled queries of every (count/8)-th instance
+    # (timed on the host cores); the same values give the batch's sampled accuracy
+    errs, cpu = [], None
+    if not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        c_pairs, c_s = 0.0, 0.0
+        for i in range(0, len(inst), max(1, len(inst) // 8)):
+            X, Q, a = inst[i]
+            idx = np.arange(0, Q.shape[0], max(1, Q.shape[0] // 16))
+            tq = time.perf_counter()
+            ref = oracle.kde(X, Q[idx], a, threads=threads)
+            c_s += time.perf_counter() - tq
+            c_pairs += float(X.shape[0] * len(idx))
+            errs.append(float(np.max(oracle.rel_err(outs[i].cpu().numpy()[idx], ref))))
+        cpu = {"value": c_pairs / c_s, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{len(errs)} instances (every {max(1, len(inst) // 8)}th), every "
+                         f"(m/16)-th query against all of the instance's points; {c_s:.1f} s"}
     recomputed = sum(k.last_recomputed() for k in kdes)
-    line = {"metric": METRIC, "value": pairs * args.steps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["batched"], "instances": len(inst), "pairs_per_step": pairs,
-                       "forms": sorted({k.form for k in kdes}), "l2": "flushed between steps (512 MiB write)"},
-            "plan_s": plan_s, "datagen_s": gen_s, "gpu_launches": int(launches),
-            "recomputed_fp32_queries": int(recomputed), "max_rel_err_sampled": max(errs), "clocks": clk,
-            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}
-    print(json.dumps(line), flush=True)
+    # form roofline of the whole batch: the slower of one ex2 per pair and each width's
+    # 2 (3 Kp + 16) MMA flops per pair at the measured dense FP16/bf16 peak
+    peaks, peak_src = load_peaks()
+    mhz = clk.get("sm_mhz") or 2070.0
+    r_ex2 = EX2_PER_SM_CLK * sm_count(0) * mhz * 1e6
+    flops = sum(2.0 * (3 * _kp(X.shape[1]) + 16) * X.shape[0] * Q.shape[0] for X, Q, _ in inst
+                if _kp(X.shape[1]))
+    t_ex2, t_mma = pairs / r_ex2, flops / (peaks["bf16_tflops"] * 1e12)
+    ms = total_ms / steps
+    roof = {"bound": "alu" if t_ex2 >= t_mma else "tensor", "roofline_ms": 1e3 * max(t_ex2, t_mma),
+            "frac": 1e3 * max(t_ex2, t_mma) / ms, "ex2_ms": 1e3 * t_ex2, "mma_ms": 1e3 * t_mma,
+            "note": "whole-batch form roofline (one ex2 per pair at 32/SM/clk x SMs x sampled clock; "
+                    "2 (3 Kp + 16) MMA flops per pair at the measured burst FP16/bf16 peak, "
+                    f"{peak_src}); the FP32 recompute of flagged queries is not in it"}
+    forms = sorted({k.form for k in kdes})
     for k in kdes:
         k.close()
+    return {"value": pairs * steps / (total_ms * 1e-3), "ms_per_step": ms, "pairs": pairs, "instances": len(inst),
+            "forms": forms, "plan_s": plan_s, "datagen_s": gen_s,
+            "gpu_launches": int(launches), "recomputed_fp32_queries": int(recomputed),
+            "max_rel_err_sampled": max(errs) if errs else None, "cpu_baseline": cpu, "clocks": clk, "roofline": roof,
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms)}}
+
+
+def run_batched(args):
+    r = measure_batched(args, args.steps, args.warmup, args.count)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batched"], "instances": r["instances"], "pairs_per_step": r["pairs"],
+                       "forms": r["forms"], "l2": "flushed between steps (512 MiB write)"},
+            **{k: r[k] for k in ("plan_s", "datagen_s", "gpu_launches", "recomputed_fp32_queries",
+                                 "max_rel_err_sampled", "cpu_baseline", "roofline", "clocks", "step_ms")}}
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -1135,6 +1185,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the large (n=2e6, d=64) object of the default line")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched (256 instances) object of the default line")
     ap.add_argument("--acc-queries", type=int, default=None, help="cap on the oracle sample used for the accuracy")
     ap.add_argument("--profile-one-step", action="store_true",
                     help="bracket one untimed step with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
