@@ -69,6 +69,28 @@ def test_batch_matches_solo_and_oracle(lib):
         k.close()
 
 
+def test_batch_uneven_widths_share_one_launch(lib):
+    """The one launch splits its CTAs by each width's share of the work: a width with a
+    single tiny instance (one unit) beside a width with a large one still gets its CTA,
+    and both match the oracle."""
+    import torch
+    from paper_2407_07096_gb300.kde import ExactGaussianKDE, query_batch
+    mix_big = G.make_mixture(91, 5, 128, -4.0, 4.0, 1.0)
+    mix_small = G.make_mixture(92, 5, 8, -4.0, 4.0, 1.0)
+    inst = [(G.sample(mix_big, 1, 60000, "data"), G.sample(mix_big, 1, 1500, "query"), 0.02),
+            (G.sample(mix_small, 2, 200, "data"), G.sample(mix_small, 2, 1, "query"), 0.5)]
+    kdes = [ExactGaussianKDE(X, a) for X, _, a in inst]
+    Qs = [torch.from_numpy(Q).cuda() for _, Q, _ in inst]
+    outs = query_batch(kdes, Qs)
+    torch.cuda.synchronize()
+    for (X, Q, a), o in zip(inst, outs):
+        idx = np.arange(0, Q.shape[0], max(1, Q.shape[0] // 64))
+        got = o.cpu().numpy()[idx]
+        assert oracle.rel_err(got, oracle.kde(X, Q[idx], a)).max() <= TOL
+    for k in kdes:
+        k.close()
+
+
 def test_batch_argument_checks(lib):
     import torch
     from paper_2407_07096_gb300 import _lib as L
